@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused freezing LB time step (MLUPS, all three
+D2Q9 populations) on GB300, with roofline, CPU-baseline and end-to-end figures.
+
+A bench "step" is one time step of the whole lattice. The default workload is
+the 1024 x 1024 drop with 8 bubbles on a cold wall (FP32 storage): each step
+moves 268 MB, more than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(independent lattices, no collective on the data path: weak scaling); rank 0
+prints one JSON line with the aggregate over ranks and the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (all 3 populations) & % HBM peak; FP16-store/batched vs plain FP32"
+BYTES_PER_LU_FP32 = 256  # 27 populations + 5 carried fields, read + write, FP32
+WORKLOAD = "bubble_drop_1024x1024_fp32"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1024, help="lattice size of the bubble drop")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self, want: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            backend = os.environ.get("LBM_BENCH_BACKEND", "nccl")
+            if backend == "nccl":
+                import torch
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            if self.pg.get_backend() == "nccl":
+                import torch
+                self.pg.barrier(device_ids=[torch.cuda.current_device()])
+            else:
+                self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(per_rank_sites_steps: float, per_rank_ms: float, dist: Dist):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    total = dist.sum(per_rank_sites_steps)
+    ms = dist.max(per_rank_ms)
+    return total / (ms * 1e-3) / 1e6, ms
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_s: float = 0.1):
+        self.idx = gpu_index
+        self.period = period_s
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _one(self):
+        try:
+            r = subprocess.run(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                               timeout=5)
+            vals = [v.strip() for v in r.stdout.strip().split(",")]
+            if len(vals) >= 7:
+                self.samples.append(vals)
+        except Exception:
+            pass
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._one()
+            self._stop.wait(self.period)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+        self._one()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for s in self.samples for j in range(4)
+                          if s[3 + j].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("lbm_kernels.cu", "lbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_2403_16122_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"step_fp32_{workload}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+kernel_source:\s*([0-9a-f]+)", txt)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(n: int, target_s: float, steps=None):
+    """Time the FP64 oracle on the bubble-drop lattice of size n. Returns
+    (MLUPS, steps, seconds, cores)."""
+    import oracle
+    from paper_2403_16122_gb300 import inputs
+
+    p, phi0, T0 = inputs.bubbles_drop(n=n)
+    o = oracle.Oracle(p).init(phi0, T0)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    if steps is None:
+        steps = max(1, int(target_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt / 1e6, steps, dt, 1
+
+
+def run_reference(args, dist: Dist):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    if dist.rank != 0:
+        return 0
+    import oracle
+    from paper_2403_16122_gb300 import inputs
+
+    oracle.build()
+    n = args.n
+    p, phi0, T0 = inputs.bubbles_drop(n=n)
+    o = oracle.Oracle(p).init(phi0, T0)
+    t0 = time.perf_counter()
+    o.step(1)
+    per = time.perf_counter() - t0
+    # bound the whole run to a few minutes: shrink the per-step sample if needed
+    if per * (args.steps + args.warmup) > 150.0:
+        n = 256
+        p, phi0, T0 = inputs.bubbles_drop(n=n)
+        o = oracle.Oracle(p).init(phi0, T0)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = n * n * args.steps / dt / 1e6
+    sample = f"{args.steps} oracle steps of the bubble drop at {n}x{n} (FP64, one core)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "sample_n": n},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    from paper_2403_16122_gb300 import build as lbm_build
+    from paper_2403_16122_gb300 import inputs, lbm
+
+    if dist.rank == 0 or not os.path.exists(lbm.LIB_PATH):
+        lbm_build.build()
+    dist.barrier()
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    n = args.n
+    p, phi0, T0 = inputs.bubbles_drop(n=n)
+    sites = n * n
+    lat = lbm.Lattice([p], device=dev)
+    stream = lat.stream
+    lat.init(phi0, T0)
+
+    # warm-up
+    if args.warmup:
+        lat.step(args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+
+    launches0 = lat.launch_count
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        start.record(stream)
+        lat.step(args.steps)
+        end.record(stream)
+        end.synchronize()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    launches = lat.launch_count - launches0
+    obs = lat.observables(check=False)
+
+    value, ms_max = aggregate(sites * args.steps, ms, dist)
+    ms_per_step = ms_max / args.steps
+
+    # roofline of the dominant kernel (the fused step), from the same events
+    peak, peak_kind = measured_hbm_peak()
+    achieved = BYTES_PER_LU_FP32 * sites / (ms / args.steps * 1e-3) / 1e9
+    traffic = profiled_traffic(WORKLOAD)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": BYTES_PER_LU_FP32 * sites}
+
+    # end to end through the C-ABI with host buffers: upload the fields from
+    # pinned memory, then per step one time step and a read of the observables
+    e2e = None
+    if not args.no_e2e:
+        k_e2e = max(1, min(args.steps, 2000))
+        ph = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        tt = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        ph.numpy()[:] = phi0
+        tt.numpy()[:] = T0
+        lat2 = lbm.Lattice([p], device=dev)
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        lat2.init(ph.numpy(), tt.numpy())
+        for _ in range(k_e2e):
+            lbm.lbm_step(lat2.handle, 1)
+            lbm.lbm_observables(lat2.handle, 0, check=False)
+        dt = time.perf_counter() - t0
+        ev, _ = aggregate(sites * k_e2e, dt * 1e3, dist)
+        e2e = {"value": ev, "unit": "MLUPS", "h2d_bytes_per_step": 16 * sites / k_e2e,
+               "d2h_bytes_per_step": 8 * lbm.LBM_OBS_COUNT, "steps": k_e2e,
+               "what": "lbm_init_fields from pinned host phi0/T0, then per step lbm_step(1) + "
+                       "lbm_observables (device-to-host read, synchronising)"}
+        lat2.close()
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        rate, st, sec, cores = oracle_rate(n, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{st} FP64 oracle steps of the {n}x{n} bubble drop ({sec:.1f} s, one core)"}
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": n, "ny": n, "sites": sites,
+                       "storage": "fp32", "bubbles": 8, "parallelism": f"replicas{dist.world}",
+                       "l2": "inputs larger than L2 (268 MB moved per step)",
+                       "bytes_per_lu": BYTES_PER_LU_FP32},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "observables": {"solid": obs[1], "volume": obs[0], "nonfinite": obs[10]},
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    dist = Dist(args.gpus)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, dist)
+        return run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

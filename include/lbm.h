@@ -1,0 +1,170 @@
+/*
+ * lbm.h -- C-ABI of liblbmfreeze, the GB300 (sm_103a) time step of the
+ * phase-field lattice Boltzmann method for freezing with volume change of
+ * Huang, Wang, Chai & Shi, "Phase-field based lattice Boltzmann method for
+ * containerless freezing" (arXiv 2403.16122).
+ *
+ * One time step advances three D2Q9 distribution sets together (Section 3):
+ *   g  -- conservative Allen-Cahn phase field (Eqs. 21-26),
+ *   h  -- total-enthalpy temperature field with the liquid-fraction closure
+ *         (Eqs. 8-9, 27-29),
+ *   f  -- pressure-based flow with the phase-change mass source and the
+ *         solid-region forcing (Eqs. 19-20, 30-36),
+ * with the isotropic stencils of Eq. 38 and the wetting ghost layer of
+ * Eqs. 39-41. All of a step runs in one fused CUDA kernel per launch.
+ *
+ * Conventions (shared with every function below):
+ *   - Lattice units, dx = dt = 1. A lattice has nx * ny sites; site (x, y)
+ *     has host index y * nx + x.
+ *   - Host distribution arrays ("pops") hold 27 planes of nx*ny doubles in the
+ *     order g_0..g_8, h_0..h_8, f_0..f_8; c_1..c_4 point E, N, W, S and
+ *     c_5..c_8 point NE, NW, SW, SE (Eq. 23). They are post-collision values.
+ *   - Host carried-field arrays ("aux") hold 5 planes of nx*ny doubles:
+ *     f_s, (phi u)_x, (phi u)_y, p, S of the last completed step.
+ *   - A non-periodic axis has a wall at both ends, half a link outside the
+ *     first and last lattice rows/columns.
+ *   - Return codes are LBM_OK or one of the negative LBM_E* values; no call
+ *     aborts the process. Device faults surface as LBM_ECUDA.
+ *
+ * Ownership: the caller owns the device workspace passed to lbm_create (the
+ * library never allocates device memory) and every host array; host arrays
+ * are read or written during the call and never retained. The handle itself
+ * is host memory owned by the library until lbm_destroy.
+ *
+ * Thread safety: a handle is used by one host thread at a time. All device
+ * work is queued on the stream given to lbm_create.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK          0
+#define LBM_EINVAL     -1  /* invalid argument or parameter set              */
+#define LBM_ENOMEM     -2  /* workspace smaller than lbm_workspace_size      */
+#define LBM_ECUDA      -3  /* a CUDA call failed (launch, copy or fault)      */
+#define LBM_ETIMEOUT   -4  /* a device-side wait gave up (batched launches)  */
+#define LBM_EUNSTABLE  -5  /* non-finite fields found by the last reduction  */
+#define LBM_ESTATE     -6  /* call out of order (e.g. step before init)      */
+
+/* Storage format of the distribution sets in device memory. Arithmetic is
+   FP32 in every format. */
+#define LBM_STORE_FP32  0
+#define LBM_STORE_FP16  1  /* deviations from the local rest equilibrium    */
+#define LBM_STORE_BF16  2
+
+/* Problem statement of one lattice (Sections 4.1-4.3). */
+typedef struct lbm_params {
+    int32_t nx, ny;                 /* lattice size, >= 3 each                */
+    int32_t periodic_x, periodic_y; /* 1 periodic, 0 walls at both ends       */
+    int32_t dirichlet_x_lo, dirichlet_x_hi;  /* per wall: 1 temperature held  */
+    int32_t dirichlet_y_lo, dirichlet_y_hi;  /* at T_w, 0 adiabatic           */
+    int32_t st_mask_liquid;         /* 1: surface tension times (1 - f_s)     */
+    int32_t reserved;               /* set to 0                               */
+    double W;            /* interface width (Eq. 3), > 0                      */
+    double sigma;        /* surface tension (Eq. 13), >= 0                    */
+    double mobility;     /* M (Eq. 2), > 0; tau_g = M / c_s^2 + 1/2           */
+    double tau_f_liquid; /* flow relaxation time of the liquid, > 1/2         */
+    double tau_h;        /* enthalpy relaxation time (Eq. 27), > 1/2          */
+    double rho_l;        /* liquid density, > 0                               */
+    double rho_ratio_lg; /* rho_l / rho_g, > 0                                */
+    double rho_ratio_sl; /* rho_s / rho_l, > 0                                */
+    double mu_ratio_lg;  /* mu_l / mu_g, > 0                                  */
+    double Ste;          /* Stefan number (Eq. 42), > 0                       */
+    double Cp, Cp_ref;   /* heat capacity, reference heat capacity (Eq. 28)   */
+    double T_m, T_w;     /* melting and wall temperature, T_w < T_m           */
+    double theta_deg;    /* wall contact angle (Eq. 39), in (0, 180)          */
+    double pc_ramp;      /* width in phi of the window where phase change
+                            switches on (solid forms only in liquid), > 0     */
+} lbm_params;
+
+/* Observables of the most recent step of an instance (index into the
+   record filled by lbm_observables); sums in FP64 over all sites. */
+#define LBM_OBS_VOLUME          0   /* sum phi (drop volume)               */
+#define LBM_OBS_SOLID           1   /* sum f_s (solid volume)              */
+#define LBM_OBS_ENTHALPY        2   /* sum H                               */
+#define LBM_OBS_MASS            3   /* sum rho                             */
+#define LBM_OBS_CONDENSED_MASS  4   /* sum f_s rho_s + (1 - f_s) phi rho_l  */
+#define LBM_OBS_MDOT            5   /* sum mdot (mass source, Eq. 19)      */
+#define LBM_OBS_PHI_MDOT        6   /* sum phi * mdot                      */
+#define LBM_OBS_SOLID_COL       7   /* sum_y f_s on column x = nx / 2      */
+#define LBM_OBS_SOLID_ROW       8   /* sum_x f_s on row y = ny / 2         */
+#define LBM_OBS_UMAX            9   /* max |u|                             */
+#define LBM_OBS_NONFINITE      10   /* sites with a non-finite field       */
+#define LBM_OBS_COUNT          11
+
+typedef struct lbm_handle lbm_handle;
+
+/* Device workspace (bytes) that lbm_create needs for n_inst lattices with
+   parameters p[0..n_inst-1] in the given storage format. Returns LBM_EINVAL
+   for bad arguments. Host only; touches no device. */
+int lbm_workspace_size(const lbm_params* p, int32_t n_inst, int32_t storage,
+                       uint64_t* bytes);
+
+/* Create a handle over n_inst independent lattices (the paper's problem
+   statement per lattice, Section 4). d_workspace is caller-owned device
+   memory of at least lbm_workspace_size bytes, 256-byte aligned; the library
+   carves every device buffer from it and never allocates. cuda_stream is a
+   cudaStream_t (NULL for the legacy default stream). Uploads the tile and
+   instance tables (host-to-device copies on the stream). On success *out
+   holds the handle; the fields still need lbm_init_fields. */
+int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage,
+               void* d_workspace, uint64_t workspace_bytes, void* cuda_stream,
+               lbm_handle** out);
+
+/* Start instance `inst` at rest (u = 0, p = 0) with every distribution at its
+   equilibrium (Eqs. 24, 28, 31) for the host fields phi0 and T0 (nx*ny
+   doubles each, read during the call). The material starts liquid-like:
+   H = Cp T0 + L (Eq. 8). Runs an initialisation kernel on the stream. */
+int lbm_init_fields(lbm_handle* h, int32_t inst, const double* phi0,
+                    const double* T0);
+
+/* Advance every instance by n >= 0 time steps (streaming, the three
+   collisions of Eqs. 21, 27, 30 and the carried fields). Asynchronous on the
+   stream; the last step of the call also reduces the observables. Launch
+   errors return LBM_ECUDA; device-side faults surface at the next
+   synchronising call. */
+int lbm_step(lbm_handle* h, int64_t n);
+
+/* Copy the observables record (LBM_OBS_COUNT doubles) of instance `inst`
+   from the last step to out. Synchronises the stream. Returns LBM_EUNSTABLE
+   (with the record filled) when any field was non-finite. */
+int lbm_observables(lbm_handle* h, int32_t inst, double* out);
+
+/* Observables of every instance: out holds n_inst * LBM_OBS_COUNT doubles.
+   Synchronises the stream. */
+int lbm_observables_all(lbm_handle* h, double* out);
+
+/* Read back instance `inst`: pops (27*nx*ny doubles) and aux (5*nx*ny
+   doubles), either may be NULL. Values are the stored post-collision
+   distributions converted to double. Synchronises the stream. Used for
+   parity checks and checkpoints. */
+int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux);
+
+/* Overwrite instance `inst` with host pops/aux (layouts as lbm_get_state;
+   both required). Resumes exactly from a lbm_get_state of FP32 storage. */
+int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
+                  const double* aux);
+
+/* Number of time steps taken since the last lbm_init_fields of instance 0. */
+int64_t lbm_step_count(const lbm_handle* h);
+
+/* Number of kernel launches the library queued since the handle was created
+   (every kernel, including initialisation and reductions). */
+int64_t lbm_launch_count(const lbm_handle* h);
+
+/* Release the handle (host memory only; the workspace stays the caller's).
+   Waits for queued work on the stream first. NULL is accepted. */
+void lbm_destroy(lbm_handle* h);
+
+/* Static description of a return code. */
+const char* lbm_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,388 @@
+// lbm_api.cu -- host side of the C-ABI declared in include/lbm.h: parameter
+// checks, the workspace layout, tile tables, launches and state transfer.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbmk::Inst;
+using lbmk::Tile;
+
+namespace {
+
+constexpr int kTileMinSites = 32 * 4;  // smallest supported tile (sizes the partials)
+constexpr uint64_t kAlign = 256;
+
+uint64_t align_up(uint64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+bool valid_params(const lbm_params& p) {
+    if (p.nx < 3 || p.ny < 3) return false;
+    if ((p.periodic_x != 0 && p.periodic_x != 1) || (p.periodic_y != 0 && p.periodic_y != 1)) return false;
+    if ((long long)pitch_of(p.nx) * p.ny * 27 >= (1LL << 31)) return false;  // 32-bit plane offsets
+    if (!(p.W > 0) || !(p.sigma >= 0) || !(p.mobility > 0)) return false;
+    if (!(p.tau_f_liquid > 0.5) || !(p.tau_h > 0.5)) return false;
+    if (!(p.rho_l > 0) || !(p.rho_ratio_lg > 0) || !(p.rho_ratio_sl > 0)) return false;
+    if (!(p.mu_ratio_lg > 0) || !(p.Ste > 0) || !(p.Cp > 0) || !(p.Cp_ref > 0)) return false;
+    if (!(p.T_w < p.T_m)) return false;
+    if (!(p.theta_deg > 0 && p.theta_deg < 180)) return false;
+    if (!(p.pc_ramp > 0)) return false;
+    if (!isfinite(p.T_m) || !isfinite(p.T_w) || !isfinite(p.sigma)) return false;
+    return true;
+}
+
+int elem_size(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
+
+struct Layout {
+    uint64_t inst_off, tile_off, part_off, obs_off, stage_off;
+    std::vector<uint64_t> pop_off[2], aux_off[2];
+    uint64_t total;
+    int max_tiles, max_sites;
+};
+
+int max_tiles_of(const lbm_params& p) {
+    // tiles of the smallest supported shape (32 x 4)
+    return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
+}
+
+Layout make_layout(const lbm_params* p, int n, int storage) {
+    Layout L;
+    uint64_t off = 0;
+    L.max_tiles = 0;
+    L.max_sites = 0;
+    for (int k = 0; k < n; ++k) {
+        L.max_tiles += max_tiles_of(p[k]);
+        L.max_sites = std::max(L.max_sites, p[k].nx * p[k].ny);
+    }
+    L.inst_off = off; off = align_up(off + sizeof(Inst) * (uint64_t)n);
+    L.tile_off = off; off = align_up(off + sizeof(Tile) * (uint64_t)L.max_tiles);
+    L.part_off = off; off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)L.max_tiles);
+    L.obs_off = off;  off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)n);
+    L.stage_off = off; off = align_up(off + sizeof(double) * 2 * (uint64_t)L.max_sites);
+    for (int b = 0; b < 2; ++b) {
+        L.pop_off[b].resize(n);
+        L.aux_off[b].resize(n);
+    }
+    for (int k = 0; k < n; ++k) {
+        const uint64_t plane = (uint64_t)pitch_of(p[k].nx) * p[k].ny;
+        for (int b = 0; b < 2; ++b) {
+            L.pop_off[b][k] = off; off = align_up(off + plane * 27 * elem_size(storage));
+            L.aux_off[b][k] = off; off = align_up(off + plane * 5 * sizeof(float));
+        }
+    }
+    L.total = off;
+    (void)kTileMinSites;
+    return L;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    std::vector<lbm_params> params;
+    int n_inst = 0;
+    int storage = 0;
+    int tx = 32, ty = 8;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    Layout layout;
+    std::vector<Inst> inst;
+    std::vector<Tile> tiles;
+    Inst* d_inst = nullptr;
+    Tile* d_tiles = nullptr;
+    double* d_part = nullptr;
+    double* d_obs = nullptr;
+    double* d_stage = nullptr;
+    int parity = 0;
+    int64_t steps = 0;
+    int64_t launches = 0;
+    bool initialised = false;
+    bool have_obs = false;
+    std::vector<double> init_L;  // double L per instance (state conversion)
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    (void)e;
+    return LBM_ECUDA;
+}
+
+void fill_inst(lbm_handle* h, int k) {
+    const lbm_params& p = h->params[k];
+    const double cs2 = 1.0 / 3.0;
+    Inst I;
+    memset(&I, 0, sizeof(I));
+    I.nx = p.nx; I.ny = p.ny; I.pitch = pitch_of(p.nx);
+    I.flags = (p.periodic_x ? lbmk::kPeriodicX : 0) | (p.periodic_y ? lbmk::kPeriodicY : 0) |
+              (p.dirichlet_x_lo ? lbmk::kDirXlo : 0) | (p.dirichlet_x_hi ? lbmk::kDirXhi : 0) |
+              (p.dirichlet_y_lo ? lbmk::kDirYlo : 0) | (p.dirichlet_y_hi ? lbmk::kDirYhi : 0) |
+              (p.st_mask_liquid ? lbmk::kStMask : 0);
+    I.plane = (long long)I.pitch * p.ny;
+    for (int b = 0; b < 2; ++b) {
+        I.pop[b] = h->ws + h->layout.pop_off[b][k];
+        I.aux[b] = reinterpret_cast<float*>(h->ws + h->layout.aux_off[b][k]);
+    }
+    const double L = p.Cp * (p.T_m - p.T_w) / p.Ste;  // Eq. 42
+    const double tau_g = p.mobility / cs2 + 0.5;
+    const double rho_g = p.rho_l / p.rho_ratio_lg, rho_s = p.rho_l * p.rho_ratio_sl;
+    const double mu_l = p.rho_l * cs2 * (p.tau_f_liquid - 0.5);
+    const double pi = acos(-1.0);
+    I.L = (float)L;
+    I.Hs = (float)(p.Cp * p.T_m);
+    I.Tm = (float)p.T_m;
+    I.Cp = (float)p.Cp;
+    I.Cpref = (float)p.Cp_ref;
+    I.Tw = (float)p.T_w;
+    I.omega_g = (float)(1.0 / tau_g);
+    I.omega_h = (float)(1.0 / p.tau_h);
+    I.kappa = (float)(1.5 * p.sigma * p.W);
+    I.beta = (float)(12.0 * p.sigma / p.W);
+    I.lam_coef = (float)(4.0 / p.W);
+    I.rho_s = (float)rho_s;
+    I.rho_l = (float)p.rho_l;
+    I.rho_g = (float)rho_g;
+    I.mu_s = (float)(mu_l * p.rho_ratio_sl);
+    I.mu_l = (float)mu_l;
+    I.mu_g = (float)(mu_l / p.mu_ratio_lg);
+    I.mdot_coef = (float)(1.0 - rho_s / p.rho_l);
+    I.tan_w = (float)tan(pi / 2.0 - p.theta_deg * pi / 180.0);
+    I.inv_ramp = (float)(1.0 / p.pc_ramp);
+    h->inst[k] = I;
+    h->init_L[k] = L;
+}
+
+void build_tiles(lbm_handle* h) {
+    h->tiles.clear();
+    for (int k = 0; k < h->n_inst; ++k) {
+        const lbm_params& p = h->params[k];
+        h->inst[k].part_begin = (int)h->tiles.size();
+        for (int y0 = 0; y0 < p.ny; y0 += h->ty)
+            for (int x0 = 0; x0 < p.nx; x0 += h->tx) {
+                Tile t;
+                t.inst = k;
+                t.x0 = x0;
+                t.y0 = y0;
+                t.tw = std::min(h->tx, p.nx - x0);
+                t.th = std::min(h->ty, p.ny - y0);
+                t.part = (int)h->tiles.size();
+                h->tiles.push_back(t);
+            }
+        h->inst[k].part_end = (int)h->tiles.size();
+    }
+}
+
+int upload_tables(lbm_handle* h) {
+    cudaError_t e = cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(Inst) * h->n_inst,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemcpyAsync(h->d_tiles, h->tiles.data(), sizeof(Tile) * h->tiles.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(h->stream);  // host tables may change after return
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e);
+}
+
+bool inst_ok(const lbm_handle* h, int32_t inst) { return h && inst >= 0 && inst < h->n_inst; }
+
+}  // namespace
+
+extern "C" {
+
+int lbm_workspace_size(const lbm_params* p, int32_t n_inst, int32_t storage, uint64_t* bytes) {
+    if (!p || !bytes || n_inst < 1) return LBM_EINVAL;
+    if (storage != LBM_STORE_FP32) return LBM_EINVAL;
+    for (int k = 0; k < n_inst; ++k)
+        if (!valid_params(p[k])) return LBM_EINVAL;
+    *bytes = make_layout(p, n_inst, storage).total;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_workspace,
+               uint64_t workspace_bytes, void* cuda_stream, lbm_handle** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    uint64_t need = 0;
+    int rc = lbm_workspace_size(p, n_inst, storage, &need);
+    if (rc != LBM_OK) return rc;
+    if (!d_workspace || ((uintptr_t)d_workspace % kAlign) != 0) return LBM_EINVAL;
+    if (workspace_bytes < need) return LBM_ENOMEM;
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ENOMEM;
+    h->params.assign(p, p + n_inst);
+    h->n_inst = n_inst;
+    h->storage = storage;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ws = static_cast<char*>(d_workspace);
+    h->layout = make_layout(p, n_inst, storage);
+    h->inst.resize(n_inst);
+    h->init_L.resize(n_inst);
+    h->d_inst = reinterpret_cast<Inst*>(h->ws + h->layout.inst_off);
+    h->d_tiles = reinterpret_cast<Tile*>(h->ws + h->layout.tile_off);
+    h->d_part = reinterpret_cast<double*>(h->ws + h->layout.part_off);
+    h->d_obs = reinterpret_cast<double*>(h->ws + h->layout.obs_off);
+    h->d_stage = reinterpret_cast<double*>(h->ws + h->layout.stage_off);
+    for (int k = 0; k < n_inst; ++k) fill_inst(h, k);
+    build_tiles(h);
+    rc = upload_tables(h);
+    if (rc != LBM_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle* h, int32_t inst, const double* phi0, const double* T0) {
+    if (!inst_ok(h, inst) || !phi0 || !T0) return LBM_EINVAL;
+    const lbm_params& p = h->params[inst];
+    const size_t n = (size_t)p.nx * p.ny;
+    cudaError_t e = cudaMemcpyAsync(h->d_stage, phi0, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_stage + h->layout.max_sites, T0, n * sizeof(double),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    lbmk::InitConst c;
+    c.L = h->init_L[inst];
+    c.Hs = p.Cp * p.T_m;
+    c.Hl = p.Cp * p.T_m + c.L;
+    c.Tm = p.T_m;
+    c.Cp = p.Cp;
+    c.Cpref = p.Cp_ref;
+    c.inv_ramp = 1.0 / p.pc_ramp;
+    e = lbmk::launch_init(h->d_inst, inst, (int)n, h->storage, c, h->d_stage,
+                          h->d_stage + h->layout.max_sites, h->parity, h->stream);
+    h->launches++;
+    if (e != cudaSuccess) return cuda_fail(e);
+    // the staging area is reused by the next call: finish the copies first
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->initialised = true;
+    h->have_obs = false;
+    if (inst == 0) h->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int64_t n) {
+    if (!h || n < 0) return LBM_EINVAL;
+    if (!h->initialised) return LBM_ESTATE;
+    for (int64_t k = 0; k < n; ++k) {
+        const int obs = (k == n - 1);
+        cudaError_t e = lbmk::launch_step(h->tx, h->ty, h->storage, h->d_inst, h->d_tiles,
+                                          (int)h->tiles.size(), h->parity, obs, h->d_part, h->stream);
+        h->launches++;
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->parity ^= 1;
+        h->steps++;
+    }
+    if (n > 0) {
+        cudaError_t e = lbmk::launch_reduce(h->d_inst, h->n_inst, h->d_part, h->d_obs, h->stream);
+        h->launches++;
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->have_obs = true;
+    }
+    return LBM_OK;
+}
+
+int lbm_observables_all(lbm_handle* h, double* out) {
+    if (!h || !out) return LBM_EINVAL;
+    if (!h->have_obs) return LBM_ESTATE;
+    cudaError_t e = cudaMemcpyAsync(out, h->d_obs, sizeof(double) * lbmk::kObs * h->n_inst,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int k = 0; k < h->n_inst; ++k)
+        if (out[k * lbmk::kObs + LBM_OBS_NONFINITE] > 0) return LBM_EUNSTABLE;
+    return LBM_OK;
+}
+
+int lbm_observables(lbm_handle* h, int32_t inst, double* out) {
+    if (!inst_ok(h, inst) || !out) return LBM_EINVAL;
+    if (!h->have_obs) return LBM_ESTATE;
+    cudaError_t e = cudaMemcpyAsync(out, h->d_obs + (size_t)inst * lbmk::kObs,
+                                    sizeof(double) * lbmk::kObs, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return out[LBM_OBS_NONFINITE] > 0 ? LBM_EUNSTABLE : LBM_OK;
+}
+
+int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
+    if (!inst_ok(h, inst)) return LBM_EINVAL;
+    if (!h->initialised) return LBM_ESTATE;
+    const lbm_params& p = h->params[inst];
+    const Inst& I = h->inst[inst];
+    const size_t n = (size_t)p.nx * p.ny;
+    std::vector<float> tp((size_t)27 * n), ta((size_t)5 * n);
+    cudaError_t e = cudaMemcpy2DAsync(tp.data(), p.nx * sizeof(float), I.pop[h->parity],
+                                      I.pitch * sizeof(float), p.nx * sizeof(float),
+                                      (size_t)27 * p.ny, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(ta.data(), p.nx * sizeof(float), I.aux[h->parity],
+                              I.pitch * sizeof(float), p.nx * sizeof(float), (size_t)5 * p.ny,
+                              cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const double L = h->init_L[inst];
+    if (pops) {
+        for (size_t k = 0; k < (size_t)27 * n; ++k) pops[k] = tp[k];
+        for (size_t k = 0; k < n; ++k) pops[9 * n + k] += L * (1.0 - (double)ta[k]);  // h_0
+    }
+    if (aux)
+        for (size_t k = 0; k < (size_t)5 * n; ++k) aux[k] = ta[k];
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
+    if (!inst_ok(h, inst) || !pops || !aux) return LBM_EINVAL;
+    const lbm_params& p = h->params[inst];
+    const Inst& I = h->inst[inst];
+    const size_t n = (size_t)p.nx * p.ny;
+    std::vector<float> tp((size_t)27 * n), ta((size_t)5 * n);
+    for (size_t k = 0; k < (size_t)5 * n; ++k) ta[k] = (float)aux[k];
+    for (size_t k = 0; k < (size_t)27 * n; ++k) tp[k] = (float)pops[k];
+    const double L = h->init_L[inst];
+    for (size_t k = 0; k < n; ++k) tp[9 * n + k] = (float)(pops[9 * n + k] - L * (1.0 - (double)ta[k]));
+    cudaError_t e = cudaMemcpy2DAsync(I.pop[h->parity], I.pitch * sizeof(float), tp.data(),
+                                      p.nx * sizeof(float), p.nx * sizeof(float), (size_t)27 * p.ny,
+                                      cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(I.aux[h->parity], I.pitch * sizeof(float), ta.data(),
+                              p.nx * sizeof(float), p.nx * sizeof(float), (size_t)5 * p.ny,
+                              cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->initialised = true;
+    h->have_obs = false;
+    return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }
+
+int64_t lbm_launch_count(const lbm_handle* h) { return h ? h->launches : -1; }
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+const char* lbm_error_string(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument or parameter set";
+        case LBM_ENOMEM: return "workspace smaller than lbm_workspace_size";
+        case LBM_ECUDA: return "CUDA call failed";
+        case LBM_ETIMEOUT: return "device-side wait timed out";
+        case LBM_EUNSTABLE: return "non-finite fields";
+        case LBM_ESTATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// lbm_internal.h -- device-side records and launch entry points shared by the
+// kernel and host-API translation units of liblbmfreeze (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+constexpr int kObs = 11;  // observables per instance (LBM_OBS_COUNT)
+
+// Bits of Inst::flags.
+enum : int {
+    kPeriodicX = 1 << 0,
+    kPeriodicY = 1 << 1,
+    kDirXlo = 1 << 2,
+    kDirXhi = 1 << 3,
+    kDirYlo = 1 << 4,
+    kDirYhi = 1 << 5,
+    kStMask = 1 << 6,
+};
+
+// One lattice as the kernels see it. Populations of set s (0 g, 1 h, 2 f) and
+// direction i live in plane 9*s + i; a plane holds ny rows of `pitch`
+// elements. In FP32 storage the rest population h_0 is stored shifted by
+// -L (1 - f_s) of the same site and step, which keeps every stored value O(1)
+// (the latent part of H is carried by the f_s plane instead).
+struct Inst {
+    int nx, ny, pitch, flags;
+    long long plane;          // elements per plane
+    void* pop[2];             // 27 planes, ping-pong buffers
+    float* aux[2];            // 5 planes: f_s, (phi u)_x, (phi u)_y, p, S
+    int part_begin, part_end; // observable partials of this lattice's tiles
+    // physics, single precision
+    float L, Hs, Tm, Cp, Cpref, Tw;
+    float omega_g, omega_h;          // 1 / tau
+    float kappa, beta, lam_coef;     // lam_coef = 4 / W
+    float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef;
+    float tan_w, inv_ramp;
+    float pad[3];
+};
+
+// One CTA's tile: lattice `inst`, origin (x0, y0), extent tw x th, and the
+// slot of its observable partials.
+struct Tile {
+    int inst, x0, y0, tw, th, part;
+};
+
+// Launch one time step over every tile (grid = n_tiles CTAs) in stream s.
+// parity selects the source buffer; obs != 0 also writes per-tile partials.
+cudaError_t launch_step(int tx, int ty, int storage, const Inst* d_inst,
+                        const Tile* d_tiles, int n_tiles, int parity, int obs,
+                        double* d_partials, cudaStream_t s);
+
+// Reduce per-tile partials into one record per lattice (grid = n_inst).
+cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partials,
+                          double* d_obs, cudaStream_t s);
+
+// Double-precision constants of the equilibrium initialisation.
+struct InitConst {
+    double L, Hs, Hl, Tm, Cp, Cpref, inv_ramp;
+};
+
+// Equilibrium initialisation of lattice `inst` (nx*ny sites) from phi0/T0
+// (device doubles, nx*ny each) into buffer `parity`.
+cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage,
+                        InitConst c, const double* d_phi0, const double* d_T0,
+                        int parity, cudaStream_t s);
+
+// Supported tile shapes (TX x TY threads, one site per thread).
+bool tile_supported(int tx, int ty);
+
+}  // namespace lbmk

@@ -1,0 +1,570 @@
+// lbm_kernels.cu -- sm_103a kernels of the freezing LB time step
+// (arXiv 2403.16122, Section 3): one fused pull-stream + collide kernel over
+// the three D2Q9 populations, the equilibrium initialisation, and the FP64
+// observable reduction.
+//
+// Fused step, per CTA tile of TX x TY sites (one thread per site):
+//   phase A  every thread pulls g, h, f of its own site (Section 3, streaming
+//            with half-way bounce-back / anti-bounce-back at walls) and forms
+//            H, f_s (Eqs. 8-9), mdot (Eq. 19), phi (Eq. 26) and rho (Eq. 1);
+//            phi and rho go to shared memory.
+//   phase B  the one-cell ring around the tile (and, next to a wall, the two
+//            extra cells per wall row that the wetting ghost needs) is pulled
+//            the same way by the first threads; the lagged p and S of the ring
+//            are staged too.
+//   phase C  ring cells behind a wall get their ghost values: the wetting
+//            condition for phi (Eqs. 39-41), a copy of the adjacent lattice
+//            value for rho, p and S.
+//   phase D  every thread evaluates the isotropic stencils (Eq. 38) from shared
+//            memory, the chemical potential and forces (Eqs. 11-12), the flow
+//            macroscopics (Eqs. 33-36), the three BGK collisions with their
+//            source terms (Eqs. 21, 25, 27, 30) and stores the post-collision
+//            populations and carried fields to the other buffer.
+// Time levels match the CPU reference: grad p and grad S use the previous
+// step's p and S; d_t(phi u) is a backward difference (Eq. 37).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbmk {
+namespace {
+
+constexpr float kW0 = 4.0f / 9.0f, kW1 = 1.0f / 9.0f, kW2 = 1.0f / 36.0f;
+__host__ __device__ constexpr int CX(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int CY(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int OPP(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+__host__ __device__ constexpr float WGT(int i) { return i == 0 ? kW0 : (i <= 4 ? kW1 : kW2); }
+
+static_assert(OPP(1) == 3 && OPP(2) == 4 && OPP(3) == 1 && OPP(4) == 2, "opp axis");
+static_assert(OPP(5) == 7 && OPP(6) == 8 && OPP(7) == 5 && OPP(8) == 6, "opp diag");
+
+__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
+
+// Mixing rule, Eq. 1, with phi clamped to [0, 1].
+__device__ __forceinline__ float mix3(float fs, float phi, float zs, float zl, float zg) {
+    float ph = clamp01(phi);
+    float liq = 1.0f - fs;
+    return fs * zs + liq * (ph * zl + (1.0f - ph) * zg);
+}
+
+// ---------------------------------------------------------------------------
+// Storage access (FP32)
+// ---------------------------------------------------------------------------
+struct Lat {
+    const float* __restrict__ A;  // source populations (27 planes)
+    const float* __restrict__ Aaux;
+    long long plane;
+    int nx, ny, pitch, flags;
+};
+
+__device__ __forceinline__ float ldA(const Lat& l, int plane, int idx) {
+    return __ldg(l.A + (long long)plane * l.plane + idx);
+}
+__device__ __forceinline__ float ldAux(const Lat& l, int k, int idx) {
+    return __ldg(l.Aaux + (long long)k * l.plane + idx);
+}
+
+// Pull of set `set` (0 g, 1 h, 2 f) at lattice site (x, y): v[i] is the
+// population arriving along c_i. Sources behind a wall are replaced by the
+// half-way bounce-back of the site's own opposite population; for h at a
+// Dirichlet wall by anti-bounce-back -h + 2 w_i Cp_ref T_w (Section 4.1).
+// h_0 is returned as stored (shifted, see Inst).
+template <int SET>
+__device__ __forceinline__ void pull_set(const Lat& l, int x, int y, float abb, float v[9]) {
+    const int own = y * l.pitch + x;
+    v[0] = ldA(l, 9 * SET, own);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        int xs = x - CX(i), ys = y - CY(i);
+        bool wall = false, dir = false;
+        if (xs < 0) {
+            if (l.flags & kPeriodicX) xs += l.nx;
+            else { wall = true; dir |= (l.flags & kDirXlo) != 0; }
+        } else if (xs >= l.nx) {
+            if (l.flags & kPeriodicX) xs -= l.nx;
+            else { wall = true; dir |= (l.flags & kDirXhi) != 0; }
+        }
+        if (ys < 0) {
+            if (l.flags & kPeriodicY) ys += l.ny;
+            else { wall = true; dir |= (l.flags & kDirYlo) != 0; }
+        } else if (ys >= l.ny) {
+            if (l.flags & kPeriodicY) ys -= l.ny;
+            else { wall = true; dir |= (l.flags & kDirYhi) != 0; }
+        }
+        if (!wall) {
+            v[i] = ldA(l, 9 * SET + i, ys * l.pitch + xs);
+        } else {
+            float b = ldA(l, 9 * SET + OPP(i), own);
+            if (SET == 1 && dir) b = -b + 2.0f * WGT(i) * abb;
+            v[i] = b;
+        }
+    }
+}
+
+struct Phys {
+    float L, Hs, Tm, Cp, Cpref, Tw, omega_g, omega_h, kappa, beta, lam_coef;
+    float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef, tan_w, inv_ramp;
+};
+
+__device__ __forceinline__ Phys load_phys(const Inst& I) {
+    Phys P;
+    P.L = I.L; P.Hs = I.Hs; P.Tm = I.Tm; P.Cp = I.Cp; P.Cpref = I.Cpref; P.Tw = I.Tw;
+    P.omega_g = I.omega_g; P.omega_h = I.omega_h; P.kappa = I.kappa; P.beta = I.beta;
+    P.lam_coef = I.lam_coef; P.rho_s = I.rho_s; P.rho_l = I.rho_l; P.rho_g = I.rho_g;
+    P.mu_s = I.mu_s; P.mu_l = I.mu_l; P.mu_g = I.mu_g; P.mdot_coef = I.mdot_coef;
+    P.tan_w = I.tan_w; P.inv_ramp = I.inv_ramp;
+    return P;
+}
+
+// Local macroscopic values at a site from its pulled g and h (phase A/B).
+struct Macro {
+    float Hp;    // H - L (1 - f_s^{n-1}) (shifted total enthalpy)
+    float fs, fsp, mdot, phi, rho;
+};
+
+__device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], const float h[9],
+                                             float fsp) {
+    Macro m;
+    float phihat = 0.0f, Hp = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { phihat += g[i]; Hp += h[i]; }
+    // Eq. 9a on the shifted enthalpy: (H - H_s)/L = (H' - H_s)/L + 1 - f_s^{n-1}.
+    float fl = clamp01((Hp - P.Hs) / P.L + (1.0f - fsp));
+    float chi = clamp01((phihat - 0.5f) * P.inv_ramp + 0.5f);
+    float fs = chi * (1.0f - fl);
+    float mdot = P.mdot_coef * (fs - fsp);               // Eq. 19
+    float phi = phihat / (1.0f - 0.5f * mdot);          // Eq. 26
+    m.Hp = Hp; m.fs = fs; m.fsp = fsp; m.mdot = mdot; m.phi = phi;
+    m.rho = mix3(fs, phi, P.rho_s, P.rho_l, P.rho_g);   // Eq. 1
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of the observables (FP64)
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void block_reduce_obs(double v[kObs], double* __restrict__ out) {
+    __shared__ double red[NT / 32][kObs];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kObs; ++j) {
+        double x = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (j == 9) ? fmax(x, y) : x + y;
+        }
+        v[j] = x;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) red[warp][j] = v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x < kObs) {
+        const int j = threadIdx.x;
+        double acc = red[0][j];
+        for (int w = 1; w < NT / 32; ++w) acc = (j == 9) ? fmax(acc, red[w][j]) : acc + red[w][j];
+        out[j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel
+// ---------------------------------------------------------------------------
+template <int TX, int TY, bool OBS>
+__global__ void __launch_bounds__(TX * TY)
+step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int parity,
+          double* __restrict__ partials) {
+    constexpr int NT = TX * TY;
+    constexpr int SW = TX + 4;                  // shared row width (2-cell halo)
+    constexpr int SH = TY + 4;
+    __shared__ float s_phi[SH * SW], s_rho[SH * SW], s_p[SH * SW], s_S[SH * SW];
+
+    const Tile T = tiles[blockIdx.x];
+    const Inst& I = insts[T.inst];
+    const Phys P = load_phys(I);
+    Lat l;
+    l.A = static_cast<const float*>(I.pop[parity]);
+    l.Aaux = I.aux[parity];
+    l.plane = I.plane; l.nx = I.nx; l.ny = I.ny; l.pitch = I.pitch; l.flags = I.flags;
+    float* __restrict__ B = static_cast<float*>(I.pop[parity ^ 1]);
+    float* __restrict__ Baux = I.aux[parity ^ 1];
+    const float abb = P.Cpref * P.Tw;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int tw = T.tw, th = T.th, x0 = T.x0, y0 = T.y0;
+    const bool active = tx < tw && ty < th;
+    const int x = x0 + tx, y = y0 + ty;
+    auto SI = [](int ox, int oy) { return (oy + 2) * SW + (ox + 2); };
+
+    // ---- phase A: own site ----
+    float g[9], h[9], f[9];
+    Macro m;
+    float phiux_p = 0.f, phiuy_p = 0.f;
+    if (active) {
+        const int own = y * l.pitch + x;
+        pull_set<0>(l, x, y, abb, g);
+        pull_set<1>(l, x, y, abb, h);
+        pull_set<2>(l, x, y, abb, f);
+        const float fsp = ldAux(l, 0, own);
+        phiux_p = ldAux(l, 1, own);
+        phiuy_p = ldAux(l, 2, own);
+        m = local_macro(P, g, h, fsp);
+        s_phi[SI(tx, ty)] = m.phi;
+        s_rho[SI(tx, ty)] = m.rho;
+        s_p[SI(tx, ty)] = ldAux(l, 3, own);
+        s_S[SI(tx, ty)] = ldAux(l, 4, own);
+    }
+
+    // ---- phase B: ring cells and wall extras ----
+    const bool wxlo = !(l.flags & kPeriodicX) && x0 == 0;
+    const bool wxhi = !(l.flags & kPeriodicX) && x0 + tw == l.nx;
+    const bool wylo = !(l.flags & kPeriodicY) && y0 == 0;
+    const bool wyhi = !(l.flags & kPeriodicY) && y0 + th == l.ny;
+    const int nring = 2 * (tw + 2) + 2 * th;
+    const int nent = nring + 4 * ((int)wxlo + (int)wxhi + (int)wylo + (int)wyhi);
+
+    // Entry k -> tile-relative cell (ox, oy).
+    auto entry = [&](int k, int& ox, int& oy) {
+        if (k < tw + 2) { ox = k - 1; oy = -1; return; }
+        k -= tw + 2;
+        if (k < tw + 2) { ox = k - 1; oy = th; return; }
+        k -= tw + 2;
+        if (k < th) { ox = -1; oy = k; return; }
+        k -= th;
+        if (k < th) { ox = tw; oy = k; return; }
+        k -= th;
+        // wall extras, 4 per touched wall
+        int w = k >> 2, j = k & 3;
+        int wl[4], nw = 0;
+        if (wylo) wl[nw++] = 0;
+        if (wyhi) wl[nw++] = 1;
+        if (wxlo) wl[nw++] = 2;
+        if (wxhi) wl[nw++] = 3;
+        int side = wl[w];
+        int a = (j & 1), b = (j >> 1);   // a: layer (adjacent/next), b: which end
+        if (side == 0) { ox = b ? tw + 1 : -2; oy = a; }
+        else if (side == 1) { ox = b ? tw + 1 : -2; oy = th - 1 - a; }
+        else if (side == 2) { oy = b ? th + 1 : -2; ox = a; }
+        else { oy = b ? th + 1 : -2; ox = tw - 1 - a; }
+    };
+    // Resolve a tile-relative cell to lattice coordinates; false when behind a wall.
+    auto resolve = [&](int ox, int oy, int& gx, int& gy, bool& outx, bool& outy) {
+        gx = x0 + ox; gy = y0 + oy;
+        outx = outy = false;
+        if (gx < 0 || gx >= l.nx) {
+            if (l.flags & kPeriodicX) gx = (gx + l.nx) % l.nx; else outx = true;
+        }
+        if (gy < 0 || gy >= l.ny) {
+            if (l.flags & kPeriodicY) gy = (gy + l.ny) % l.ny; else outy = true;
+        }
+        return !(outx || outy);
+    };
+
+    for (int k = tid; k < nent; k += NT) {
+        int ox, oy, gx, gy;
+        bool outx, outy;
+        entry(k, ox, oy);
+        if (resolve(ox, oy, gx, gy, outx, outy)) {
+            float gg[9], hh[9];
+            pull_set<0>(l, gx, gy, abb, gg);
+            pull_set<1>(l, gx, gy, abb, hh);
+            const int idx = gy * l.pitch + gx;
+            Macro mm = local_macro(P, gg, hh, ldAux(l, 0, idx));
+            s_phi[SI(ox, oy)] = mm.phi;
+            s_rho[SI(ox, oy)] = mm.rho;
+            if (k < nring) {
+                s_p[SI(ox, oy)] = ldAux(l, 3, idx);
+                s_S[SI(ox, oy)] = ldAux(l, 4, idx);
+            }
+        } else if (k < nring) {
+            // ghost: p and S copy the adjacent lattice value
+            int cx = min(max(x0 + ox, 0), l.nx - 1), cy = min(max(y0 + oy, 0), l.ny - 1);
+            if (!outx) cx = gx;
+            if (!outy) cy = gy;
+            const int idx = cy * l.pitch + cx;
+            s_p[SI(ox, oy)] = ldAux(l, 3, idx);
+            s_S[SI(ox, oy)] = ldAux(l, 4, idx);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase C: ghosts of phi (wetting) and rho (copy) ----
+    // Shared-memory slot of a lattice coordinate (periodic axes wrap into the
+    // tile's 2-cell halo).
+    auto lat_slot = [&](int xl, int yl) {
+        int ox = xl - x0, oy = yl - y0;
+        if (ox < -2) ox += l.nx; else if (ox > tw + 1) ox -= l.nx;
+        if (oy < -2) oy += l.ny; else if (oy > th + 1) oy -= l.ny;
+        return SI(ox, oy);
+    };
+    auto wrap_or_clamp = [](int v, int n, bool periodic) {
+        if (v >= 0 && v < n) return v;
+        if (periodic) return (v + n) % n;
+        return v < 0 ? 0 : n - 1;
+    };
+    for (int k = tid; k < nring; k += NT) {
+        int ox, oy, gx, gy;
+        bool outx, outy;
+        entry(k, ox, oy);
+        if (resolve(ox, oy, gx, gy, outx, outy)) continue;
+        const int cxl = outx ? (x0 + ox < 0 ? 0 : l.nx - 1) : gx;
+        const int cyl = outy ? (y0 + oy < 0 ? 0 : l.ny - 1) : gy;
+        s_rho[SI(ox, oy)] = s_rho[lat_slot(cxl, cyl)];
+        float ghost;
+        if (outy && !outx) {
+            const int ya = cyl, yb = (y0 + oy < 0) ? 1 : l.ny - 2;
+            const bool px = (l.flags & kPeriodicX) != 0;
+            const int xm = wrap_or_clamp(gx - 1, l.nx, px), xp = wrap_or_clamp(gx + 1, l.nx, px);
+            const float d0 = 0.5f * (s_phi[lat_slot(xp, ya)] - s_phi[lat_slot(xm, ya)]);
+            const float d1 = 0.5f * (s_phi[lat_slot(xp, yb)] - s_phi[lat_slot(xm, yb)]);
+            ghost = s_phi[lat_slot(gx, ya)] + P.tan_w * fabsf(1.5f * d0 - 0.5f * d1);
+        } else if (outx && !outy) {
+            const int xa = cxl, xb = (x0 + ox < 0) ? 1 : l.nx - 2;
+            const bool py = (l.flags & kPeriodicY) != 0;
+            const int ym = wrap_or_clamp(gy - 1, l.ny, py), yp = wrap_or_clamp(gy + 1, l.ny, py);
+            const float d0 = 0.5f * (s_phi[lat_slot(xa, yp)] - s_phi[lat_slot(xa, ym)]);
+            const float d1 = 0.5f * (s_phi[lat_slot(xb, yp)] - s_phi[lat_slot(xb, ym)]);
+            ghost = s_phi[lat_slot(xa, gy)] + P.tan_w * fabsf(1.5f * d0 - 0.5f * d1);
+        } else {
+            ghost = s_phi[lat_slot(cxl, cyl)];
+        }
+        s_phi[SI(ox, oy)] = ghost;
+    }
+    __syncthreads();
+
+    // ---- phase D: stencils, forces, collisions, store ----
+    double ob[kObs];
+    if (OBS) {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) ob[j] = 0.0;
+    }
+    if (active) {
+        const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
+        // Eq. 38 from shared memory: grad = 3 sum w c z, lap = 6 sum w (z - z0)
+        float gphx = 0.f, gphy = 0.f, lph = 0.f, grx = 0.f, gry = 0.f;
+        float gpx = 0.f, gpy = 0.f, gSx = 0.f, gSy = 0.f;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int s = SI(tx + CX(i), ty + CY(i));
+            const float w = WGT(i);
+            const float zp = s_phi[s], zr = s_rho[s], zq = s_p[s], zs = s_S[s];
+            gphx += w * CX(i) * zp; gphy += w * CY(i) * zp;
+            lph += w * (zp - phi);
+            grx += w * CX(i) * zr; gry += w * CY(i) * zr;
+            gpx += w * CX(i) * zq; gpy += w * CY(i) * zq;
+            gSx += w * CX(i) * zs; gSy += w * CY(i) * zs;
+        }
+        gphx *= 3.f; gphy *= 3.f; lph *= 6.f;
+        grx *= 3.f; gry *= 3.f; gpx *= 3.f; gpy *= 3.f; gSx *= 3.f; gSy *= 3.f;
+
+        // Eqs. 11-12 (phi_l = 1, phi_g = 0)
+        const float muphi = 4.f * P.beta * (phi - 1.f) * phi * (phi - 0.5f) - P.kappa * lph;
+        float Fx = muphi * gphx, Fy = muphi * gphy;
+        if (l.flags & kStMask) { Fx *= (1.f - fs); Fy *= (1.f - fs); }
+
+        // Eqs. 34-35: u* from the flow moments, solid forcing f = -f_s u*
+        float mx = 0.f, my = 0.f, fne0 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            mx += CX(i) * f[i];
+            my += CY(i) * f[i];
+            if (i) fne0 += f[i];
+        }
+        const float usx = (mx + 0.5f * Fx) / rho, usy = (my + 0.5f * Fy) / rho;
+        const float ffx = -fs * usx, ffy = -fs * usy;
+        const float ux = usx + 0.5f * ffx, uy = usy + 0.5f * ffy;
+        const float uu = ux * ux + uy * uy;
+
+        // Eq. 33 source terms (grad p, grad S lagged one step)
+        const float S = rho * mdot + ux * grx + uy * gry;
+        const float Ftx = Fx - gpx + (grx + gSx) * (1.f / 3.f);
+        const float Fty = Fy - gpy + (gry + gSy) * (1.f / 3.f);
+        const float uFt = ux * Ftx + uy * Fty;
+        const float mu = mix3(fs, phi, P.mu_s, P.mu_l, P.mu_g);
+        const float tau_f = mu / (rho * (1.f / 3.f)) + 0.5f;
+        const float omega_f = 1.f / tau_f;
+        const float Fpx = Fx + rho * ffx, Fpy = Fy + rho * ffy;  // F + rho f
+        const float F0 = kW0 * (S - 3.f * uFt);
+        // Eq. 36 with s_0(u) = -w_0 u.u / (2 c_s^2)
+        const float pn = (1.f / 3.f) / (1.f - kW0) *
+                         (fne0 + 0.5f * S + tau_f * F0 + rho * (-kW0 * 1.5f * uu));
+
+        // Phase field: n, lambda (Eq. 3), d_t(phi u) (Eq. 37), G_i (Eq. 25)
+        const float g2 = gphx * gphx + gphy * gphy;
+        float nx_ = 0.f, ny_ = 0.f;
+        if (g2 >= 1e-24f) { const float r = rsqrtf(g2); nx_ = gphx * r; ny_ = gphy * r; }
+        const float lam = P.lam_coef * phi * (1.f - phi);
+        const float phiux = phi * ux, phiuy = phi * uy;
+        const float ax = (phiux - phiux_p) + (1.f / 3.f) * lam * nx_;
+        const float ay = (phiuy - phiuy_p) + (1.f / 3.f) * lam * ny_;
+        const float gsrc = 1.f - 0.5f * P.omega_g;
+        const float pmd = phi * mdot;
+
+        // Enthalpy: T from Eq. 8 with f_l = 1 - f_s on the shifted enthalpy
+        const float dL = P.L * (fs - m.fsp);
+        const float T = P.Tm + (m.Hp - P.Hs + dL) / P.Cp;
+        const float cpT = P.Cp * T;
+
+        const int own = y * l.pitch + x;
+        const float fsrc = 1.f - 0.5f * omega_f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float w = WGT(i);
+            const float cu = CX(i) * ux + CY(i) * uy;
+            // g (Eqs. 21, 24, 25)
+            const float geq = w * phi * (1.f + 3.f * cu);
+            const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
+            const float gn = g[i] - P.omega_g * (g[i] - geq) + gsrc * Gi;
+            // h (Eqs. 27-28); h_0 carried shifted by -L (1 - f_s)
+            float hn;
+            if (i == 0) {
+                const float heq0 = m.Hp + dL - P.Cpref * T + kW0 * T * (P.Cpref - P.Cp * 1.5f * uu);
+                hn = (1.f - P.omega_h) * (h[0] + dL) + P.omega_h * heq0;
+            } else {
+                const float heq = w * T * (P.Cpref + P.Cp * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+                hn = h[i] - P.omega_h * (h[i] - heq);
+            }
+            // f (Eqs. 30-33)
+            const float si = w * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+            const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
+            const float cF = CX(i) * Ftx + CY(i) * Fty;
+            const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
+            const float fn = f[i] - omega_f * (f[i] - feq) + fsrc * Fi;
+            B[(long long)(i) * l.plane + own] = gn;
+            B[(long long)(9 + i) * l.plane + own] = hn;
+            B[(long long)(18 + i) * l.plane + own] = fn;
+        }
+        Baux[own] = fs;
+        Baux[l.plane + own] = phiux;
+        Baux[2 * l.plane + own] = phiuy;
+        Baux[3 * l.plane + own] = pn;
+        Baux[4 * l.plane + own] = S;
+        (void)cpT;
+
+        if (OBS) {
+            const double dphi = phi, dfs = fs;
+            ob[0] = dphi;
+            ob[1] = dfs;
+            ob[2] = (double)m.Hp + (double)P.L * (1.0 - (double)m.fsp);
+            ob[3] = rho;
+            ob[4] = dfs * P.rho_s + (1.0 - dfs) * (double)clamp01(phi) * P.rho_l;
+            ob[5] = mdot;
+            ob[6] = dphi * (double)mdot;
+            ob[7] = (x == l.nx / 2) ? dfs : 0.0;
+            ob[8] = (y == l.ny / 2) ? dfs : 0.0;
+            ob[9] = sqrt((double)uu);
+            const bool bad = !isfinite(phi) || !isfinite(m.Hp) || !isfinite(ux) ||
+                             !isfinite(uy) || !isfinite(pn);
+            ob[10] = bad ? 1.0 : 0.0;
+        }
+    }
+    if (OBS) block_reduce_obs<NT>(ob, partials + (long long)T.part * kObs);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation (double precision, then rounded to the storage format)
+// ---------------------------------------------------------------------------
+__global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
+                          const double* __restrict__ phi0, const double* __restrict__ T0,
+                          int parity) {
+    const Inst& I = insts[inst];
+    const int n = I.nx * I.ny;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int x = k % I.nx, y = k / I.nx;
+        const long long idx = (long long)y * I.pitch + x;
+        const double ph = phi0[k];
+        const double H = c.Cp * T0[k] + c.L;
+        double fl = (H - c.Hs) / c.L;
+        fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
+        double chi = (ph - 0.5) * c.inv_ramp + 0.5;
+        chi = chi < 0 ? 0 : (chi > 1 ? 1 : chi);
+        const double fs = chi * (1.0 - fl);
+        const double T = c.Tm + (H - c.Hl + c.L * fs) / c.Cp;
+        float* P = static_cast<float*>(I.pop[parity]);
+        float* A = I.aux[parity];
+        for (int i = 0; i < 9; ++i) {
+            const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+            P[(long long)i * I.plane + idx] = (float)(w * ph);                     // Eq. 24, u = 0
+            double hq = (i == 0) ? H - c.Cpref * T + w * c.Cp * T * (c.Cpref / c.Cp)
+                                 : w * c.Cp * T * (c.Cpref / c.Cp);                // Eq. 28, u = 0
+            if (i == 0) hq -= c.L * (1.0 - fs);                                    // shifted h_0
+            P[(long long)(9 + i) * I.plane + idx] = (float)hq;
+            P[(long long)(18 + i) * I.plane + idx] = 0.0f;  // Eq. 31 vanishes at p = 0, u = 0
+        }
+        A[idx] = (float)fs;
+        A[I.plane + idx] = 0.f;
+        A[2 * I.plane + idx] = 0.f;
+        A[3 * I.plane + idx] = 0.f;
+        A[4 * I.plane + idx] = 0.f;
+    }
+}
+
+// Per-lattice reduction of tile partials in a fixed order (deterministic).
+__global__ void reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
+                           double* __restrict__ out) {
+    const Inst& I = insts[blockIdx.x];
+    const int j = threadIdx.x;
+    if (j >= kObs) return;
+    double acc = 0.0;
+    for (int p = I.part_begin; p < I.part_end; ++p) {
+        const double v = partials[(long long)p * kObs + j];
+        acc = (j == 9) ? fmax(acc, v) : acc + v;
+    }
+    out[(long long)blockIdx.x * kObs + j] = acc;
+}
+
+template <int TX, int TY>
+cudaError_t launch_tile(const Inst* d_inst, const Tile* d_tiles, int n_tiles, int parity,
+                        int obs, double* d_partials, cudaStream_t s) {
+    if (obs)
+        step_fp32<TX, TY, true><<<n_tiles, TX * TY, 0, s>>>(d_inst, d_tiles, parity, d_partials);
+    else
+        step_fp32<TX, TY, false><<<n_tiles, TX * TY, 0, s>>>(d_inst, d_tiles, parity, d_partials);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tile_supported(int tx, int ty) {
+    return (tx == 32 && ty == 8) || (tx == 32 && ty == 4) || (tx == 64 && ty == 4) ||
+           (tx == 32 && ty == 16);
+}
+
+cudaError_t launch_step(int tx, int ty, int storage, const Inst* d_inst, const Tile* d_tiles,
+                        int n_tiles, int parity, int obs, double* d_partials, cudaStream_t s) {
+    if (storage != 0) return cudaErrorNotSupported;
+    if (tx == 32 && ty == 8) return launch_tile<32, 8>(d_inst, d_tiles, n_tiles, parity, obs, d_partials, s);
+    if (tx == 32 && ty == 4) return launch_tile<32, 4>(d_inst, d_tiles, n_tiles, parity, obs, d_partials, s);
+    if (tx == 64 && ty == 4) return launch_tile<64, 4>(d_inst, d_tiles, n_tiles, parity, obs, d_partials, s);
+    if (tx == 32 && ty == 16) return launch_tile<32, 16>(d_inst, d_tiles, n_tiles, parity, obs, d_partials, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partials,
+                          double* d_obs, cudaStream_t s) {
+    reduce_obs<<<n_inst, 32, 0, s>>>(d_inst, d_partials, d_obs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage, InitConst c,
+                        const double* d_phi0, const double* d_T0, int parity, cudaStream_t s) {
+    if (storage != 0) return cudaErrorNotSupported;
+    const int threads = 256;
+    int blocks = (n_sites + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    init_fp32<<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -1,0 +1,83 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+entry point that include/lbm.h declares; host-only calls validate their
+arguments. No compute call runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2403_16122_gb300 import build as lbm_build
+from paper_2403_16122_gb300 import inputs, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lbm_build.build()
+    return lbm.load()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_\w+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(lbm.SYMBOLS)
+
+
+def test_params_struct_layout_matches_header():
+    txt = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    body = txt[txt.index("typedef struct lbm_params"):txt.index("} lbm_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for typ, names in re.findall(r"(int32_t|double)\s+([^;]+);", body):
+        for n in names.split(","):
+            fields.append((n.strip(), typ))
+    got = [(n, "int32_t" if t is ctypes.c_int32 else "double") for n, t in lbm.lbm_params._fields_]
+    assert got == fields
+    assert ctypes.sizeof(lbm.lbm_params) == 10 * 4 + 16 * 8
+
+
+def test_workspace_size_host_only(lib):
+    p, _, _ = inputs.stefan()
+    n1 = lbm.lbm_workspace_size([p])
+    # 2 buffers x (27 + 5) planes of 256 x 8 floats at least
+    assert n1 >= 2 * 32 * 256 * 8 * 4
+    n2 = lbm.lbm_workspace_size([p, p])
+    assert n2 > 1.9 * n1 - 4096
+
+
+@pytest.mark.parametrize("bad", [dict(nx=2), dict(tau_h=0.5), dict(mobility=0.0),
+                                 dict(theta_deg=0.0), dict(T_w=0.5), dict(Ste=-1.0),
+                                 dict(pc_ramp=0.0), dict(periodic_x=2)])
+def test_invalid_parameters_rejected(lib, bad):
+    p = inputs.params(**bad)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_workspace_size([p])
+    assert e.value.code == lbm.LBM_EINVAL
+
+
+def test_unsupported_storage_rejected(lib):
+    p = inputs.params()
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_size([p], storage=7)
+
+
+def test_error_strings(lib):
+    for code in range(-6, 1):
+        assert lbm.lbm_error_string(code)
+    assert "unknown" in lbm.lbm_error_string(-99)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_step_count(None) == -1
+    lib.lbm_destroy(None)

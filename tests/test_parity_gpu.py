@@ -1,0 +1,169 @@
+"""GPU parity: the CUDA time step (through the C-ABI) against the FP64 oracle on
+the same seeded inputs, element by element, at sizes the oracle finishes in
+seconds (several tiles and ragged tails), plus one-step checks at the full
+benchmark size and the edge cases of the boundary (tiny periodic lattices,
+closed boxes with corners, every wall type)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_16122_gb300 import inputs
+from parity_util import compare_state, gpu_run, max_abs, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_16122_gb300 import build
+    build.build()
+
+
+def _both(oracle_mod, p, phi0, T0, steps):
+    lat = gpu_run([p], [(phi0, T0)], steps)
+    o = oracle_run(oracle_mod, p, phi0, T0, steps)
+    return lat, o
+
+
+def test_stefan_1000_steps(oracle_mod):
+    """Three-phase Stefan problem, 256 x 8, the 1000-step FP32 bar."""
+    p, phi0, T0 = inputs.stefan()
+    lat, o = _both(oracle_mod, p, phi0, T0, 1000)
+    d = compare_state(lat.get_state(), o.get_state())
+    print("stefan 1000:", d)
+    ob_g, ob_o = lat.observables(), o.observables()
+    assert ob_g["solid"] == pytest.approx(ob_o["solid"], rel=1e-5)
+    assert ob_g["volume"] == pytest.approx(ob_o["volume"], rel=1e-6)
+    assert ob_g["solid"] > 30
+
+
+def test_sessile_ragged_1000_steps(oracle_mod):
+    """Sessile drop on the cold wall (density ratio 1000, viscosity ratio 100,
+    wetting at 90 deg) on a 100 x 70 lattice: ragged tiles on both axes."""
+    p, phi0, T0 = inputs.sessile(nx=100, ny=70, R=24.0)
+    lat, o = _both(oracle_mod, p, phi0, T0, 1000)
+    d = compare_state(lat.get_state(), o.get_state())
+    print("sessile 100x70:", d)
+    assert o.observables()["solid"] > 10
+
+
+@pytest.mark.parametrize("theta", [45.0, 120.0])
+def test_wetting_and_closed_box(oracle_mod, theta):
+    """Closed box (corners on every side), Dirichlet at two walls, wetting at
+    an angle other than 90 deg, perturbed fields, 300 steps."""
+    p = inputs.params(nx=45, ny=37, periodic_x=0, periodic_y=0, dirichlet_y_lo=1,
+                      dirichlet_x_hi=1, theta_deg=theta, rho_ratio_lg=100.0,
+                      mu_ratio_lg=30.0, rho_ratio_sl=0.92)
+    phi0, T0 = inputs.random_state(p, seed=11)
+    lat, o = _both(oracle_mod, p, phi0, T0, 300)
+    d = compare_state(lat.get_state(), o.get_state())
+    print("closed box", theta, d)
+
+
+def test_bubbles_masked_surface_tension(oracle_mod):
+    """Drop with bubbles, surface tension restricted to the liquid."""
+    p, phi0, T0 = inputs.bubbles_drop(n=128, n_bub=3, r_lo=4.0, r_hi=8.0, seed=5)
+    lat, o = _both(oracle_mod, p, phi0, T0, 500)
+    compare_state(lat.get_state(), o.get_state())
+
+
+@pytest.mark.parametrize("nx,ny,px,py", [(5, 7, 1, 1), (3, 3, 1, 1), (33, 9, 1, 0),
+                                         (9, 40, 0, 1), (3, 5, 0, 0)])
+def test_small_and_odd_lattices(oracle_mod, nx, ny, px, py):
+    """Tiny periodic wraps, single-column tails, walls on tiny grids."""
+    p = inputs.params(nx=nx, ny=ny, periodic_x=px, periodic_y=py, dirichlet_y_lo=1 - py,
+                      dirichlet_x_lo=1 - px, theta_deg=70.0)
+    phi0, T0 = inputs.random_state(p, seed=nx * 100 + ny)
+    lat, o = _both(oracle_mod, p, phi0, T0, 200)
+    compare_state(lat.get_state(), o.get_state())
+
+
+def test_set_state_roundtrip_and_resume(oracle_mod):
+    """lbm_set_state / lbm_get_state round-trip FP32 state exactly, and a resumed
+    run matches an uninterrupted one bit for bit."""
+    p, phi0, T0 = inputs.sessile(nx=64, ny=48, R=16.0, theta_deg=70.0)
+    a = gpu_run([p], [(phi0, T0)], 50)
+    s = a.get_state()
+    b = gpu_run([p], [(phi0, T0)], 0)
+    b.set_state(*s)
+    s2 = b.get_state()
+    assert np.array_equal(s[0], s2[0]) and np.array_equal(s[1], s2[1])
+    a.step(30)
+    b.step(30)
+    sa, sb = a.get_state(), b.get_state()
+    assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+
+
+def test_one_step_from_common_state(oracle_mod):
+    """Start both sides from the same (oracle) state and take one step: the
+    difference is FP32 rounding of a single update."""
+    p, phi0, T0 = inputs.sessile(nx=80, ny=60, R=20.0, theta_deg=60.0)
+    o = oracle_run(oracle_mod, p, phi0, T0, 200)
+    pops, aux = o.get_state()
+    lat = gpu_run([p], [(phi0, T0)], 0)
+    lat.set_state(pops, aux)
+    lat.step(1)
+    o.step(1)
+    compare_state(lat.get_state(), o.get_state(), tol_pops=2e-6, tol_aux=2e-6)
+
+
+def test_full_size_bubbles_one_step(oracle_mod):
+    """The benchmark workload (1024 x 1024 drop with 8 bubbles) in the launch
+    configuration the benchmark times: run 20 steps on the GPU, hand the GPU
+    state to the oracle, and compare one further step over every site."""
+    p, phi0, T0 = inputs.bubbles_drop()
+    lat = gpu_run([p], [(phi0, T0)], 20)
+    pops, aux = lat.get_state()
+    o = oracle_mod.Oracle(p)
+    o.set_state(pops, aux)
+    o.step(1)
+    lat.step(1)
+    compare_state(lat.get_state(), o.get_state(), tol_pops=2e-6, tol_aux=2e-6)
+
+
+def test_observables_match_oracle(oracle_mod):
+    p, phi0, T0 = inputs.sessile(nx=96, ny=64, R=24.0, theta_deg=100.0)
+    lat, o = _both(oracle_mod, p, phi0, T0, 400)
+    g, r = lat.observables(), o.observables()
+    for k in ("volume", "solid", "enthalpy", "mass", "condensed_mass", "solid_col", "solid_row"):
+        assert g[k] == pytest.approx(r[k], rel=1e-5, abs=1e-6), k
+    for k in ("mdot", "phi_mdot"):
+        assert g[k] == pytest.approx(r[k], abs=1e-5), k
+    assert g["umax"] == pytest.approx(r["umax"], rel=1e-3, abs=1e-7)
+    assert g["nonfinite"] == 0.0
+
+
+def test_batched_instances_equal_single_runs(oracle_mod):
+    """Several lattices of uneven size in one handle advance exactly as each
+    does alone (same arithmetic, same tiles)."""
+    cases = inputs.batched_sweep(n_inst=3, seed=3, sizes=(40, 64, 96))
+    lat = gpu_run([c[0] for c in cases], [(c[1], c[2]) for c in cases], 60)
+    for k, (p, phi0, T0) in enumerate(cases):
+        one = gpu_run([p], [(phi0, T0)], 60)
+        a, b = lat.get_state(k), one.get_state()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    allobs = lat.observables_all()
+    assert allobs.shape == (3, 11)
+
+
+def test_step_zero_and_call_order():
+    from paper_2403_16122_gb300 import lbm
+
+    p, phi0, T0 = inputs.stefan(nx=40)
+    lat = lbm.Lattice([p])
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(1)
+    assert e.value.code == lbm.LBM_ESTATE
+    lat.init(phi0, T0)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.observables()
+    assert e.value.code == lbm.LBM_ESTATE
+    s0 = lat.get_state()
+    lat.step(0)
+    s1 = lat.get_state()
+    assert np.array_equal(s0[0], s1[0])
+    n0 = lat.launch_count
+    lat.step(3)
+    assert lat.launch_count == n0 + 4  # 3 steps + 1 reduction
+    assert lat.step_count == 3
