@@ -364,7 +364,7 @@ def run_ours(args, dist: Dist):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
-            "observables": {"solid": obs[1], "volume": obs[0], "nonfinite": obs[10]},
+            "observables": {k: obs[k] for k in ("solid", "volume", "nonfinite")},
         }
         print(json.dumps(line), flush=True)
     lat.close()

@@ -20,7 +20,8 @@
  *     order g_0..g_8, h_0..h_8, f_0..f_8; c_1..c_4 point E, N, W, S and
  *     c_5..c_8 point NE, NW, SW, SE (Eq. 23). They are post-collision values.
  *   - Host carried-field arrays ("aux") hold 5 planes of nx*ny doubles:
- *     f_s, (phi u)_x, (phi u)_y, p, S of the last completed step.
+ *     f_l (liquid fraction), (phi u)_x, (phi u)_y, p, S of the last
+ *     completed step.
  *   - A non-periodic axis has a wall at both ends, half a link outside the
  *     first and last lattice rows/columns.
  *   - Return codes are LBM_OK or one of the negative LBM_E* values; no call
@@ -80,6 +81,8 @@ typedef struct lbm_params {
     double theta_deg;    /* wall contact angle (Eq. 39), in (0, 180)          */
     double pc_ramp;      /* width in phi of the window where phase change
                             switches on (solid forms only in liquid), > 0     */
+    double normal_eps;   /* interface-normal regularisation, > 0:
+                            n = grad phi / sqrt(|grad phi|^2 + eps^2)         */
 } lbm_params;
 
 /* Observables of the most recent step of an instance (index into the
@@ -146,7 +149,10 @@ int lbm_observables_all(lbm_handle* h, double* out);
 int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux);
 
 /* Overwrite instance `inst` with host pops/aux (layouts as lbm_get_state;
-   both required). Resumes exactly from a lbm_get_state of FP32 storage. */
+   both required). A lbm_get_state / lbm_set_state round trip of FP32 storage
+   restores every stored value exactly, except that h_0 (kept on the device
+   shifted by -L f_l) can move by one float ulp where its shifted value is
+   below ~1e-8, i.e. by at most ~2e-15. */
 int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
                   const double* aux);
 

@@ -65,6 +65,7 @@ class OracleParams(ctypes.Structure):
         ("Cp", ctypes.c_double), ("Cp_ref", ctypes.c_double),
         ("T_m", ctypes.c_double), ("T_w", ctypes.c_double),
         ("theta_deg", ctypes.c_double), ("pc_ramp", ctypes.c_double),
+        ("normal_eps", ctypes.c_double),
     ]
 
 

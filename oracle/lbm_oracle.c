@@ -10,27 +10,42 @@
  *   R2  Local tau_f = mu / (rho c_s^2) + 1/2 with rho, mu from Eq. 1;
  *       mu_l = rho_l c_s^2 (tau_f_liquid - 1/2), mu_g = mu_l / (mu_l/mu_g),
  *       mu_s = mu_l rho_s / rho_l. phi is clamped to [0, 1] inside Eq. 1.
- *   R3  Solid forms only in the liquid (Section 2). The latent heat L is carried
- *       everywhere (gas counts as liquid-like, f_l = 1, H = Cp T + L), and the
- *       solid fraction is f_s = chi(phihat) (1 - f_l(H)) with f_l(H) from Eq. 9a
- *       and chi a linear ramp from 0 to 1 over phihat in
+ *   R3  The thermal model of Section 2.2 carries no phase field: T and the
+ *       liquid fraction f_l follow from H alone by Eqs. 8-9, everywhere. The
+ *       gas starts liquid-like (f_l = 1, H = Cp T + L), so the latent heat is
+ *       uniform as Section 2.2 assumes when it drops div(rho u Delta H).
+ *       Solid forms only in the liquid (Section 2): the solid fraction that
+ *       enters Eq. 1, Eq. 19 and the solid forcing is f_s = chi(phihat) (1 - f_l),
+ *       chi a linear ramp from 0 to 1 over phihat in
  *       [1/2 - pc_ramp/2, 1/2 + pc_ramp/2], phihat = sum_i g_i.
- *       T follows from Eq. 8 with f_l := 1 - f_s; for chi = 1 this is Eq. 9b.
  *   R4  Pure substance: T_s = T_l = T_m, H_s = Cp T_m, H_l = Cp T_m + L (the
  *       second "H_s" after Eq. 9b is read as H_l).
  *   R5  div u in Eqs. 25-26 is mdot (Eq. 19): phi = sum g / (1 - mdot/2),
  *       and the last term of G_i is w_i phi mdot.
- *   R6  df_s/dt in mdot (Eq. 19) is the backward difference f_s^n - f_s^{n-1}.
+ *   R6  df_s/dt in mdot (Eq. 19) is the change of f_s by phase change over one
+ *       step, chi(phihat^n) (f_l^{n-1} - f_l^n): the solid does not move, so
+ *       only freezing or melting of the liquid content changes it.
  *   R7  The pressure gradient and the gradient of S inside F~ (Eq. 33) use the
  *       previous step's p and S (carried planes), which breaks the p <-> grad p
  *       circularity of Eq. 36.
- *   R8  n = grad phi / |grad phi| is set to 0 where |grad phi|^2 < 1e-24.
+ *   R8  n = grad phi / |grad phi| is undefined where grad phi vanishes, which
+ *       happens at extrema of phi in the bulk where lambda is not zero; there
+ *       the unit normal flips with the sign of an arbitrarily small gradient.
+ *       The normal is regularised as n = grad phi / sqrt(|grad phi|^2 + eps^2)
+ *       (eps = normal_eps, 1e-3 by default: |n| > 0.99999 across the interface
+ *       core where |grad phi| ~ 1/W, and lambda n stays Lipschitz in the bulk).
  *   R9  "c_s^2 div S" in F~ is read as c_s^2 grad S (S is a scalar, dt = 1);
  *       the tensor of Eq. 33 is (u F~ + F~ u).
  *   R10 With st_mask_liquid the surface tension is (1 - f_s) mu_phi grad phi
  *       (Section 4.3 writes f_s; the stated purpose, a force only at the
  *       bubble-liquid interface, needs the liquid fraction).
- *   R11 The tau Delta t F_0 term of Eq. 36 is kept with the local tau_f.
+ *   R11 The F_0 term of Eq. 36 is the first-order non-equilibrium part of the
+ *       rest population that Eq. 30 implies, (tau_f - 1/2) Delta t F_0, with
+ *       the local tau_f. (Eq. 36 prints tau Delta t F_0; a Chapman-Enskog
+ *       expansion of Eq. 30, whose source carries 1 - 1/(2 tau_f), gives
+ *       f_0 - f_0^eq = -tau dt d_t f_0^eq + (tau - 1/2) dt F_0, and the printed
+ *       coefficient makes bulk phi depart from 1 without bound near a
+ *       freezing wall.)
  *   R12 The solid interaction force of Eq. 35 is f = f_s (0 - u*) (u_s = 0),
  *       u = u* + f/2, and rho f enters F_i (Eq. 33).
  *   R13 Wetting ghosts (Eqs. 39-41): for a wall below row 0 the ghost at
@@ -43,7 +58,8 @@
  *       h_i = -h_ibar^* + 2 w_i Cp_ref T_w ; no-flux (g) and no-slip (f) walls
  *       use half-way bounce-back (Section 4.1).
  *   Parity unpinned (no closed form separates the alternatives; the choice
- *   defines the scheme): R7, R9, R11, R12 and the ramp width of R3.
+ *   defines the scheme): R7, R9, R12, the ramp width of R3 and the eps of R8.
+ *   The carried planes are f_l, (phi u)_x, (phi u)_y, p, S.
  */
 #include "lbm_oracle.h"
 
@@ -62,7 +78,7 @@ static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static const double CS2 = 1.0 / 3.0; /* c_s^2 = c^2 / 3 */
 
 enum { SET_G = 0, SET_H = 1, SET_F = 2 };
-enum { AUX_FS = 0, AUX_PHIUX, AUX_PHIUY, AUX_P, AUX_S, AUX_COUNT };
+enum { AUX_FL = 0, AUX_PHIUX, AUX_PHIUY, AUX_P, AUX_S, AUX_COUNT };
 
 struct oracle_state {
     oracle_params p;
@@ -74,6 +90,7 @@ struct oracle_state {
     double *aux, *aux_new; /* 5 carried planes          */
     double *pre;           /* 27 planes, post-streaming (pre-collision) */
     double *fld;           /* 10 planes of the step's macroscopic fields */
+    double *pre_fl;        /* liquid fraction of the step */
 };
 
 static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
@@ -154,14 +171,24 @@ void oracle_source_G(double phi, double mdot, double dtx, double dty,
         out[i] = WT[i] * (CX[i] * ax + CY[i] * ay) / CS2 + WT[i] * phi * mdot;
 }
 
-/* Eqs. 8-9 with readings R3/R4. */
+/* Eqs. 8-9 with readings R3/R4: liquid fraction and temperature from H. */
+static void thermal_closure(const oracle_state* s, double H, double* fl, double* T) {
+    double f = clamp01((H - s->Hs) / s->L);               /* Eq. 9a */
+    *fl = f;
+    *T = s->p.T_m + (H - s->Hs - s->L * f) / s->p.Cp;     /* Eq. 9b */
+}
+
+/* R3: solid only in the liquid content of a site. */
+static double solid_fraction(const oracle_state* s, double fl, double phihat) {
+    double chi = clamp01((phihat - 0.5) / s->p.pc_ramp + 0.5);
+    return chi * (1.0 - fl);
+}
+
 void oracle_closure(const oracle_state* s, double H, double phihat, double* fs,
                     double* T) {
-    double fl = clamp01((H - s->Hs) / s->L);               /* Eq. 9a */
-    double chi = clamp01((phihat - 0.5) / s->p.pc_ramp + 0.5); /* R3 */
-    double f = chi * (1.0 - fl);
-    *fs = f;
-    *T = s->p.T_m + (H - s->Hl + s->L * f) / s->p.Cp;      /* Eq. 8, f_l = 1 - f_s */
+    double fl;
+    thermal_closure(s, H, &fl, T);
+    *fs = solid_fraction(s, fl, phihat);
 }
 
 /* Eq. 1 (reading R2: phi clamped to [0, 1]). */
@@ -281,6 +308,7 @@ static int valid(const oracle_params* p) {
     if (!(p->T_w < p->T_m)) return 0;
     if (!(p->theta_deg > 0 && p->theta_deg < 180)) return 0;
     if (!(p->pc_ramp > 0)) return 0;
+    if (!(p->normal_eps > 0)) return 0;
     return 1;
 }
 
@@ -311,7 +339,8 @@ int oracle_create(const oracle_params* p, oracle_state** out) {
     s->aux = calloc(na, sizeof(double));
     s->aux_new = calloc(na, sizeof(double));
     s->fld = calloc((size_t)ORACLE_FLD_COUNT * s->n, sizeof(double));
-    if (!s->pop || !s->pop_new || !s->pre || !s->aux || !s->aux_new || !s->fld) {
+    s->pre_fl = calloc((size_t)s->n, sizeof(double));
+    if (!s->pop || !s->pop_new || !s->pre || !s->aux || !s->aux_new || !s->fld || !s->pre_fl) {
         oracle_destroy(s);
         return -2;
     }
@@ -322,7 +351,7 @@ int oracle_create(const oracle_params* p, oracle_state** out) {
 void oracle_destroy(oracle_state* s) {
     if (!s) return;
     free(s->pop); free(s->pop_new); free(s->pre);
-    free(s->aux); free(s->aux_new); free(s->fld);
+    free(s->aux); free(s->aux_new); free(s->fld); free(s->pre_fl);
     free(s);
 }
 
@@ -340,8 +369,9 @@ int oracle_init(oracle_state* s, const double* phi0, const double* T0) {
     double eq[9];
     for (int64_t k = 0; k < n; ++k) {
         double H = s->p.Cp * T0[k] + s->L;
-        double fs, T;
-        oracle_closure(s, H, phi0[k], &fs, &T);
+        double fl, T;
+        thermal_closure(s, H, &fl, &T);
+        double fs = solid_fraction(s, fl, phi0[k]);
         double rho = mix(fs, phi0[k], s->rho_s, s->p.rho_l, s->rho_g);
         oracle_geq(phi0[k], 0.0, 0.0, eq);
         for (int i = 0; i < 9; ++i) s->pop[(SET_G * 9 + i) * n + k] = eq[i];
@@ -349,7 +379,7 @@ int oracle_init(oracle_state* s, const double* phi0, const double* T0) {
         for (int i = 0; i < 9; ++i) s->pop[(SET_H * 9 + i) * n + k] = eq[i];
         oracle_feq(0.0, rho, 0.0, 0.0, eq);
         for (int i = 0; i < 9; ++i) s->pop[(SET_F * 9 + i) * n + k] = eq[i];
-        s->aux[AUX_FS * n + k] = fs;
+        s->aux[AUX_FL * n + k] = fl;
         s->aux[AUX_PHIUX * n + k] = 0.0;
         s->aux[AUX_PHIUY * n + k] = 0.0;
         s->aux[AUX_P * n + k] = 0.0;
@@ -385,7 +415,8 @@ static void step_once(oracle_state* s) {
     double* fsf = F + ORACLE_FLD_FS * n;
     double* mdf = F + ORACLE_FLD_MDOT * n;
     double* rhof = F + ORACLE_FLD_RHO * n;
-    const double* fs_prev = s->aux + AUX_FS * n;
+    double* flf = s->pre_fl;
+    const double* fl_prev = s->aux + AUX_FL * n;
     const double* phiux_prev = s->aux + AUX_PHIUX * n;
     const double* phiuy_prev = s->aux + AUX_PHIUY * n;
     const double* p_prev = s->aux + AUX_P * n;
@@ -409,13 +440,16 @@ static void step_once(oracle_state* s) {
                 H += s->pre[(SET_H * 9 + i) * n + k];      /* Eq. 29 */
                 phihat += s->pre[(SET_G * 9 + i) * n + k];
             }
-            double fs, T;
-            oracle_closure(s, H, phihat, &fs, &T);       /* Eqs. 8-9, R3 */
-            double mdot = (1.0 - s->rho_s / p->rho_l) * (fs - fs_prev[k]); /* Eq. 19, R6 */
+            double fl, T;
+            thermal_closure(s, H, &fl, &T);                /* Eqs. 8-9, R3 */
+            double chi = clamp01((phihat - 0.5) / p->pc_ramp + 0.5);
+            double fs = chi * (1.0 - fl);
+            double mdot = (1.0 - s->rho_s / p->rho_l) * chi * (fl_prev[k] - fl); /* Eq. 19, R6 */
             double ph = phihat / (1.0 - 0.5 * mdot);     /* Eq. 26, R5 */
             Hf[k] = H;
             Tf[k] = T;
             fsf[k] = fs;
+            flf[k] = fl;
             mdf[k] = mdot;
             phi[k] = ph;
             rhof[k] = mix(fs, ph, s->rho_s, p->rho_l, s->rho_g); /* Eq. 1 */
@@ -462,12 +496,13 @@ static void step_once(oracle_state* s) {
             double Fi[9];
             oracle_force_F(S, Fx + rho * ffx, Fy + rho * ffy, ux, uy, Ftx, Fty, Fi);
             double pnew = CS2 / (1.0 - WT[0]) *
-                          (fsum_ne0 + 0.5 * S + tau_f * Fi[0] + rho * s_i(0, ux, uy)); /* Eq. 36, R11 */
+                          (fsum_ne0 + 0.5 * S + (tau_f - 0.5) * Fi[0] +
+                           rho * s_i(0, ux, uy)); /* Eq. 36, R11 */
 
             /* Phase field (Eqs. 21, 24, 25, 37). */
             double g2 = gphx * gphx + gphy * gphy;
-            double nnx = 0.0, nny = 0.0;
-            if (g2 >= 1e-24) { double gm = sqrt(g2); nnx = gphx / gm; nny = gphy / gm; } /* R8 */
+            double gm = sqrt(g2 + p->normal_eps * p->normal_eps); /* R8 */
+            double nnx = gphx / gm, nny = gphy / gm;
             double lam = 4.0 * ph * (1.0 - ph) / p->W;              /* Eq. 3 */
             double phiux = ph * ux, phiuy = ph * uy;
             double dtx = phiux - phiux_prev[k], dty = phiuy - phiuy_prev[k]; /* Eq. 37 */
@@ -500,7 +535,7 @@ static void step_once(oracle_state* s) {
             }
 
             /* Carried planes for the next step. */
-            s->aux_new[AUX_FS * n + k] = fs;
+            s->aux_new[AUX_FL * n + k] = flf[k];
             s->aux_new[AUX_PHIUX * n + k] = phiux;
             s->aux_new[AUX_PHIUY * n + k] = phiuy;
             s->aux_new[AUX_P * n + k] = pnew;

@@ -14,7 +14,7 @@
  * distribution sets (Eqs. 22-23). A site (x, y) has linear index y*nx + x.
  * Distribution planes are ordered g_0..g_8, h_0..h_8, f_0..f_8 (27 planes of
  * nx*ny doubles); the carried (lagged) scalar planes are ordered
- * f_s, (phi u)_x, (phi u)_y, p, S (5 planes).
+ * f_l (liquid fraction), (phi u)_x, (phi u)_y, p, S (5 planes).
  *
  * Walls sit half-way between the last lattice row/column and a ghost layer
  * (Section 3.4). A non-periodic axis has a wall at both ends.
@@ -53,6 +53,8 @@ typedef struct oracle_params {
     double theta_deg;      /* contact angle of the wetting wall (Eq. 39)          */
     double pc_ramp;        /* width in phi of the window where phase change
                               switches on (solid forms only in the liquid)        */
+    double normal_eps;     /* regularisation of the interface normal:
+                              n = grad phi / sqrt(|grad phi|^2 + eps^2)           */
 } oracle_params;
 
 /* Observables of the most recent step (indices into the output array). */

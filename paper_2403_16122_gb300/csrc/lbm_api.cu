@@ -34,6 +34,7 @@ bool valid_params(const lbm_params& p) {
     if (!(p.T_w < p.T_m)) return false;
     if (!(p.theta_deg > 0 && p.theta_deg < 180)) return false;
     if (!(p.pc_ramp > 0)) return false;
+    if (!(p.normal_eps > 0) || !isfinite(p.normal_eps)) return false;
     if (!isfinite(p.T_m) || !isfinite(p.T_w) || !isfinite(p.sigma)) return false;
     return true;
 }
@@ -154,6 +155,7 @@ void fill_inst(lbm_handle* h, int k) {
     I.mdot_coef = (float)(1.0 - rho_s / p.rho_l);
     I.tan_w = (float)tan(pi / 2.0 - p.theta_deg * pi / 180.0);
     I.inv_ramp = (float)(1.0 / p.pc_ramp);
+    I.normal_eps2 = (float)(p.normal_eps * p.normal_eps);
     h->inst[k] = I;
     h->init_L[k] = L;
 }
@@ -331,7 +333,7 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     const double L = h->init_L[inst];
     if (pops) {
         for (size_t k = 0; k < (size_t)27 * n; ++k) pops[k] = tp[k];
-        for (size_t k = 0; k < n; ++k) pops[9 * n + k] += L * (1.0 - (double)ta[k]);  // h_0
+        for (size_t k = 0; k < n; ++k) pops[9 * n + k] += L * (double)ta[k];  // h_0 + L f_l
     }
     if (aux)
         for (size_t k = 0; k < (size_t)5 * n; ++k) aux[k] = ta[k];
@@ -347,7 +349,7 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double*
     for (size_t k = 0; k < (size_t)5 * n; ++k) ta[k] = (float)aux[k];
     for (size_t k = 0; k < (size_t)27 * n; ++k) tp[k] = (float)pops[k];
     const double L = h->init_L[inst];
-    for (size_t k = 0; k < n; ++k) tp[9 * n + k] = (float)(pops[9 * n + k] - L * (1.0 - (double)ta[k]));
+    for (size_t k = 0; k < n; ++k) tp[9 * n + k] = (float)(pops[9 * n + k] - L * (double)ta[k]);
     cudaError_t e = cudaMemcpy2DAsync(I.pop[h->parity], I.pitch * sizeof(float), tp.data(),
                                       p.nx * sizeof(float), p.nx * sizeof(float), (size_t)27 * p.ny,
                                       cudaMemcpyHostToDevice, h->stream);

@@ -23,13 +23,13 @@ enum : int {
 // One lattice as the kernels see it. Populations of set s (0 g, 1 h, 2 f) and
 // direction i live in plane 9*s + i; a plane holds ny rows of `pitch`
 // elements. In FP32 storage the rest population h_0 is stored shifted by
-// -L (1 - f_s) of the same site and step, which keeps every stored value O(1)
-// (the latent part of H is carried by the f_s plane instead).
+// -L f_l of the same site and step, which keeps every stored value O(1) (the
+// latent part of H is carried by the liquid-fraction plane instead).
 struct Inst {
     int nx, ny, pitch, flags;
     long long plane;          // elements per plane
     void* pop[2];             // 27 planes, ping-pong buffers
-    float* aux[2];            // 5 planes: f_s, (phi u)_x, (phi u)_y, p, S
+    float* aux[2];            // 5 planes: f_l, (phi u)_x, (phi u)_y, p, S
     int part_begin, part_end; // observable partials of this lattice's tiles
     // physics, single precision
     float L, Hs, Tm, Cp, Cpref, Tw;
@@ -37,7 +37,8 @@ struct Inst {
     float kappa, beta, lam_coef;     // lam_coef = 4 / W
     float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef;
     float tan_w, inv_ramp;
-    float pad[3];
+    float normal_eps2;               // squared regularisation of the normal
+    float pad[2];
 };
 
 // One CTA's tile: lattice `inst`, origin (x0, y0), extent tw x th, and the

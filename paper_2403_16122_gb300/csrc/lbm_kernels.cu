@@ -30,7 +30,15 @@
 namespace lbmk {
 namespace {
 
-constexpr float kW0 = 4.0f / 9.0f, kW1 = 1.0f / 9.0f, kW2 = 1.0f / 36.0f;
+// D2Q9 weights (Eq. 22) in single precision, chosen so that the float values
+// sum to exactly 1: w0 and w1 are the nearest floats to 4/9 and 1/9, w2 is one
+// ulp below the nearest float to 1/36 (relative error 6e-8). With the nearest
+// floats the weights sum to 1 + 7.45e-9, and every BGK collision then creates
+// omega * 7.45e-9 * phi of order parameter (and likewise enthalpy) per site
+// and step, a drift that grows linearly with time.
+constexpr float kW0 = 0x1.c71c72p-2f, kW1 = 0x1.c71c72p-4f, kW2 = 0x1.c71c70p-6f;
+static_assert((double)kW0 + 4.0 * (double)kW1 + 4.0 * (double)kW2 == 1.0,
+              "D2Q9 float weights must sum to one exactly");
 __host__ __device__ constexpr int CX(int i) {
     return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
 }
@@ -110,7 +118,7 @@ __device__ __forceinline__ void pull_set(const Lat& l, int x, int y, float abb, 
 
 struct Phys {
     float L, Hs, Tm, Cp, Cpref, Tw, omega_g, omega_h, kappa, beta, lam_coef;
-    float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef, tan_w, inv_ramp;
+    float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef, tan_w, inv_ramp, eps2;
 };
 
 __device__ __forceinline__ Phys load_phys(const Inst& I) {
@@ -119,29 +127,34 @@ __device__ __forceinline__ Phys load_phys(const Inst& I) {
     P.omega_g = I.omega_g; P.omega_h = I.omega_h; P.kappa = I.kappa; P.beta = I.beta;
     P.lam_coef = I.lam_coef; P.rho_s = I.rho_s; P.rho_l = I.rho_l; P.rho_g = I.rho_g;
     P.mu_s = I.mu_s; P.mu_l = I.mu_l; P.mu_g = I.mu_g; P.mdot_coef = I.mdot_coef;
-    P.tan_w = I.tan_w; P.inv_ramp = I.inv_ramp;
+    P.tan_w = I.tan_w; P.inv_ramp = I.inv_ramp; P.eps2 = I.normal_eps2;
     return P;
 }
 
 // Local macroscopic values at a site from its pulled g and h (phase A/B).
+// H' = H - L f_l^{n-1} is what the stored h_0 sums to (see Inst).
 struct Macro {
-    float Hp;    // H - L (1 - f_s^{n-1}) (shifted total enthalpy)
-    float fs, fsp, mdot, phi, rho;
+    float Hp;    // shifted total enthalpy H'
+    float fl, flp, fs, mdot, phi, rho;
+    bool mushy;  // H strictly between H_s and H_l: T = T_m exactly (Eq. 9b)
 };
 
 __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], const float h[9],
-                                             float fsp) {
+                                             float flp) {
     Macro m;
     float phihat = 0.0f, Hp = 0.0f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) { phihat += g[i]; Hp += h[i]; }
-    // Eq. 9a on the shifted enthalpy: (H - H_s)/L = (H' - H_s)/L + 1 - f_s^{n-1}.
-    float fl = clamp01((Hp - P.Hs) / P.L + (1.0f - fsp));
-    float chi = clamp01((phihat - 0.5f) * P.inv_ramp + 0.5f);
-    float fs = chi * (1.0f - fl);
-    float mdot = P.mdot_coef * (fs - fsp);               // Eq. 19
-    float phi = phihat / (1.0f - 0.5f * mdot);          // Eq. 26
-    m.Hp = Hp; m.fs = fs; m.fsp = fsp; m.mdot = mdot; m.phi = phi;
+    // Eq. 9a on the shifted enthalpy: (H - H_s)/L = (H' - H_s)/L + f_l^{n-1}
+    const float q = (Hp - P.Hs) / P.L + flp;
+    const float fl = clamp01(q);
+    m.mushy = q > 0.0f && q < 1.0f;
+    // solid only in the liquid content of the site
+    const float chi = clamp01((phihat - 0.5f) * P.inv_ramp + 0.5f);
+    const float fs = chi * (1.0f - fl);
+    const float mdot = P.mdot_coef * chi * (flp - fl);   // Eq. 19, phase change only
+    const float phi = phihat / (1.0f - 0.5f * mdot);    // Eq. 26
+    m.Hp = Hp; m.fl = fl; m.flp = flp; m.fs = fs; m.mdot = mdot; m.phi = phi;
     m.rho = mix3(fs, phi, P.rho_s, P.rho_l, P.rho_g);   // Eq. 1
     return m;
 }
@@ -215,10 +228,10 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
         pull_set<0>(l, x, y, abb, g);
         pull_set<1>(l, x, y, abb, h);
         pull_set<2>(l, x, y, abb, f);
-        const float fsp = ldAux(l, 0, own);
+        const float flp = ldAux(l, 0, own);
         phiux_p = ldAux(l, 1, own);
         phiuy_p = ldAux(l, 2, own);
-        m = local_macro(P, g, h, fsp);
+        m = local_macro(P, g, h, flp);
         s_phi[SI(tx, ty)] = m.phi;
         s_rho[SI(tx, ty)] = m.rho;
         s_p[SI(tx, ty)] = ldAux(l, 3, own);
@@ -395,14 +408,16 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
         const float omega_f = 1.f / tau_f;
         const float Fpx = Fx + rho * ffx, Fpy = Fy + rho * ffy;  // F + rho f
         const float F0 = kW0 * (S - 3.f * uFt);
-        // Eq. 36 with s_0(u) = -w_0 u.u / (2 c_s^2)
+        // Eq. 36 with s_0(u) = -w_0 u.u / (2 c_s^2); the F_0 correction is the
+        // first-order non-equilibrium part of f_0 that Eq. 30 implies,
+        // (tau_f - 1/2) F_0
         const float pn = (1.f / 3.f) / (1.f - kW0) *
-                         (fne0 + 0.5f * S + tau_f * F0 + rho * (-kW0 * 1.5f * uu));
+                         (fne0 + 0.5f * S + (tau_f - 0.5f) * F0 + rho * (-kW0 * 1.5f * uu));
 
         // Phase field: n, lambda (Eq. 3), d_t(phi u) (Eq. 37), G_i (Eq. 25)
-        const float g2 = gphx * gphx + gphy * gphy;
-        float nx_ = 0.f, ny_ = 0.f;
-        if (g2 >= 1e-24f) { const float r = rsqrtf(g2); nx_ = gphx * r; ny_ = gphy * r; }
+        // regularised normal n = grad phi / sqrt(|grad phi|^2 + eps^2)
+        const float rn = rsqrtf(gphx * gphx + gphy * gphy + P.eps2);
+        const float nx_ = gphx * rn, ny_ = gphy * rn;
         const float lam = P.lam_coef * phi * (1.f - phi);
         const float phiux = phi * ux, phiuy = phi * uy;
         const float ax = (phiux - phiux_p) + (1.f / 3.f) * lam * nx_;
@@ -410,9 +425,12 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
         const float gsrc = 1.f - 0.5f * P.omega_g;
         const float pmd = phi * mdot;
 
-        // Enthalpy: T from Eq. 8 with f_l = 1 - f_s on the shifted enthalpy
-        const float dL = P.L * (fs - m.fsp);
-        const float T = P.Tm + (m.Hp - P.Hs + dL) / P.Cp;
+        // Enthalpy: T from Eq. 9b on the shifted enthalpy,
+        // H - H_s - L f_l = H' - H_s + L (f_l^{n-1} - f_l); inside the mushy
+        // range the exact value is T_m (evaluating the sum there would only
+        // add the rounding of f_l times L)
+        const float dL = P.L * (m.flp - m.fl);
+        const float T = m.mushy ? P.Tm : P.Tm + (m.Hp - P.Hs + dL) / P.Cp;
         const float cpT = P.Cp * T;
 
         const int own = y * l.pitch + x;
@@ -425,7 +443,7 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
             const float geq = w * phi * (1.f + 3.f * cu);
             const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
             const float gn = g[i] - P.omega_g * (g[i] - geq) + gsrc * Gi;
-            // h (Eqs. 27-28); h_0 carried shifted by -L (1 - f_s)
+            // h (Eqs. 27-28); h_0 carried shifted by -L f_l
             float hn;
             if (i == 0) {
                 const float heq0 = m.Hp + dL - P.Cpref * T + kW0 * T * (P.Cpref - P.Cp * 1.5f * uu);
@@ -444,7 +462,7 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
             B[(long long)(9 + i) * l.plane + own] = hn;
             B[(long long)(18 + i) * l.plane + own] = fn;
         }
-        Baux[own] = fs;
+        Baux[own] = m.fl;
         Baux[l.plane + own] = phiux;
         Baux[2 * l.plane + own] = phiuy;
         Baux[3 * l.plane + own] = pn;
@@ -455,7 +473,7 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
             const double dphi = phi, dfs = fs;
             ob[0] = dphi;
             ob[1] = dfs;
-            ob[2] = (double)m.Hp + (double)P.L * (1.0 - (double)m.fsp);
+            ob[2] = (double)m.Hp + (double)P.L * (double)m.flp;
             ob[3] = rho;
             ob[4] = dfs * P.rho_s + (1.0 - dfs) * (double)clamp01(phi) * P.rho_l;
             ob[5] = mdot;
@@ -484,12 +502,9 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
         const long long idx = (long long)y * I.pitch + x;
         const double ph = phi0[k];
         const double H = c.Cp * T0[k] + c.L;
-        double fl = (H - c.Hs) / c.L;
+        double fl = (H - c.Hs) / c.L;                 // Eq. 9a
         fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
-        double chi = (ph - 0.5) * c.inv_ramp + 0.5;
-        chi = chi < 0 ? 0 : (chi > 1 ? 1 : chi);
-        const double fs = chi * (1.0 - fl);
-        const double T = c.Tm + (H - c.Hl + c.L * fs) / c.Cp;
+        const double T = c.Tm + (H - c.Hs - c.L * fl) / c.Cp;  // Eq. 9b
         float* P = static_cast<float*>(I.pop[parity]);
         float* A = I.aux[parity];
         for (int i = 0; i < 9; ++i) {
@@ -497,11 +512,11 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
             P[(long long)i * I.plane + idx] = (float)(w * ph);                     // Eq. 24, u = 0
             double hq = (i == 0) ? H - c.Cpref * T + w * c.Cp * T * (c.Cpref / c.Cp)
                                  : w * c.Cp * T * (c.Cpref / c.Cp);                // Eq. 28, u = 0
-            if (i == 0) hq -= c.L * (1.0 - fs);                                    // shifted h_0
+            if (i == 0) hq -= c.L * fl;                                            // shifted h_0
             P[(long long)(9 + i) * I.plane + idx] = (float)hq;
             P[(long long)(18 + i) * I.plane + idx] = 0.0f;  // Eq. 31 vanishes at p = 0, u = 0
         }
-        A[idx] = (float)fs;
+        A[idx] = (float)fl;
         A[I.plane + idx] = 0.f;
         A[2 * I.plane + idx] = 0.f;
         A[3 * I.plane + idx] = 0.f;

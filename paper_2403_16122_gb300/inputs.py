@@ -9,7 +9,8 @@ Parameter dictionaries carry the paper's own problem statement (Sections 4.1,
 4.2 and 4.3 of arXiv 2403.16122): lattice size, walls, relaxation times,
 density/viscosity ratios, Stefan number, rho_s/rho_l, contact angle, wall
 temperature. Values the paper leaves open are fixed here once: sigma = 0.01,
-rho_l = 1, Cp = Cp_ref = 1, T_m = 0, and a phase-change ramp width of 0.2.
+rho_l = 1, Cp = Cp_ref = 1, T_m = 0, a phase-change ramp width of 0.2 and an
+interface-normal regularisation of 1e-3.
 
 Arrays use the lattice layout [ny, nx]; site (x, y) is element [y, x]. Walls
 sit half a link outside the first and last lattice rows/columns, so a wall
@@ -32,7 +33,7 @@ BASE = dict(
     tau_f_liquid=0.8, tau_h=0.8,
     rho_l=1.0, rho_ratio_lg=10.0, rho_ratio_sl=0.9, mu_ratio_lg=10.0,
     Ste=0.1, Cp=1.0, Cp_ref=1.0, T_m=0.0, T_w=-1.0,
-    theta_deg=90.0, pc_ramp=0.2,
+    theta_deg=90.0, pc_ramp=0.2, normal_eps=1e-3,
 )
 
 

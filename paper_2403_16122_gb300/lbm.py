@@ -42,6 +42,7 @@ class lbm_params(ctypes.Structure):
         ("Cp", ctypes.c_double), ("Cp_ref", ctypes.c_double),
         ("T_m", ctypes.c_double), ("T_w", ctypes.c_double),
         ("theta_deg", ctypes.c_double), ("pc_ramp", ctypes.c_double),
+        ("normal_eps", ctypes.c_double),
     ]
 
 

@@ -244,29 +244,30 @@ def test_closure_liquid_matches_eq9(oracle_mod, Tm, Tw, Ste, Cp):
         assert H == pytest.approx(Cp * T + L * (1 - fs), abs=1e-12)
 
 
-def test_closure_gas_is_sensible_only_and_continuous(oracle_mod):
+def test_closure_temperature_ignores_phase_field_and_solid_is_masked(oracle_mod):
+    """The thermal model of Section 2.2 has no phi: T follows Eq. 9b for every
+    phihat. Solid forms only in the liquid content: f_s = 0 in gas, f_s =
+    1 - f_l in liquid, continuous in between with slope <= 1 / pc_ramp."""
     o = _state(oracle_mod)
     L = o.derived()["L"]
+    ramp = inputs.BASE["pc_ramp"]
     for H in np.linspace(-3, L + 3, 41):
-        fs, T = o.closure(H, 0.0)
-        assert fs == 0.0
-        assert T == pytest.approx((H - L) / 1.0, abs=1e-13)
-    # continuity in phihat and H, and energy consistency everywhere
-    Hs = np.linspace(-2, L + 2, 61)
-    ph = np.linspace(-0.1, 1.1, 61)
-    last = None
-    for H in Hs:
-        row = []
-        for q in ph:
+        fl, Tp = _paper_closure(H, 1.0, 0.0, L)
+        for q in (-0.05, 0.0, 0.2, 0.5 - ramp / 2):
             fs, T = o.closure(H, q)
-            assert 0.0 <= fs <= 1.0
-            assert H == pytest.approx(T + L * (1 - fs), abs=1e-12)
-            row.append((fs, T))
-        row = np.array(row)
-        assert np.abs(np.diff(row[:, 0])).max() <= 0.021 / 0.2 + 1e-12
-        if last is not None:
-            assert np.abs(row[:, 1] - last[:, 1]).max() < 0.25
-        last = row
+            assert fs == pytest.approx(0.0, abs=1e-15)
+            assert T == pytest.approx(Tp, abs=1e-12)
+        for q in (0.5 + ramp / 2, 0.8, 1.0, 1.05):
+            fs, T = o.closure(H, q)
+            assert fs == pytest.approx(1.0 - fl, abs=1e-13)
+            assert T == pytest.approx(Tp, abs=1e-12)
+    ph = np.linspace(-0.1, 1.1, 121)
+    for H in np.linspace(-2, L + 2, 31):
+        fl, _ = _paper_closure(H, 1.0, 0.0, L)
+        fs = np.array([o.closure(H, q)[0] for q in ph])
+        assert (fs >= 0).all() and (fs <= 1.0 - fl + 1e-15).all()
+        assert np.abs(np.diff(fs)).max() <= (ph[1] - ph[0]) / ramp + 1e-12
+        assert (np.diff(fs) >= -1e-15).all()  # more liquid content, more solid
 
 
 def test_derived_parameters(oracle_mod):
@@ -285,6 +286,6 @@ def test_derived_parameters(oracle_mod):
 
 def test_invalid_parameters_rejected(oracle_mod):
     for bad in (dict(nx=2), dict(tau_h=0.5), dict(mobility=0.0), dict(theta_deg=180.0),
-                dict(T_w=0.0), dict(Ste=0.0), dict(rho_ratio_lg=-1.0)):
+                dict(T_w=0.0), dict(Ste=0.0), dict(rho_ratio_lg=-1.0), dict(normal_eps=0.0)):
         with pytest.raises(oracle_mod.OracleError):
             _state(oracle_mod, **bad)

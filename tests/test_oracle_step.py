@@ -127,12 +127,13 @@ def test_thermal_diffusivity_from_tau_h(oracle_mod):
 
 
 def test_dirichlet_wall_conduction(oracle_mod):
-    """Gas between two cold walls at half-links x = -1/2 and x = nx - 1/2: the
-    slowest mode sin(pi (x + 1/2) / nx) decays at alpha (pi / nx)^2 and the
-    temperature relaxes to T_w (anti-bounce-back, Section 4.1)."""
+    """Gas between two cold walls at half-links x = -1/2 and x = nx - 1/2 with a
+    negligible latent heat (Ste = 1e5): the slowest mode sin(pi (x + 1/2) / nx)
+    decays at alpha (pi / nx)^2 and the temperature relaxes to T_w
+    (anti-bounce-back, Section 4.1)."""
     nx, ny = 40, 4
     p = inputs.params(nx=nx, ny=ny, periodic_x=0, periodic_y=1, dirichlet_x_lo=1,
-                      dirichlet_x_hi=1)
+                      dirichlet_x_hi=1, Ste=1e5)
     x, _ = inputs.coords(nx, ny)
     basis = np.sin(math.pi * (x + 0.5) / nx)
     o = run(oracle_mod, p, np.zeros((ny, nx)), np.full((ny, nx), 1.0))
@@ -184,7 +185,9 @@ def test_flat_interface_is_steady(oracle_mod):
     """phi = 1/2 + 1/2 tanh(2 d / W) satisfies grad phi = lambda n (Eqs. 2-3),
     so a flat interface at rest without freezing keeps its place: after a
     short relaxation to the lattice's own profile (within 1e-2 of the tanh) it
-    stays fixed and the flow dies out."""
+    stays fixed and the flow dies out. The regularised normal (eps = 1e-3)
+    leaves the outermost tails, where lambda < eps, to slow diffusion: less
+    than 3e-4 over 4000 steps."""
     nx, ny = 64, 4
     p = inputs.params(nx=nx, ny=ny)
     phi0 = inputs.slab(nx, ny, 16.0, 48.0, p["W"])
@@ -193,11 +196,12 @@ def test_flat_interface_is_steady(oracle_mod):
     mid = o.fields()["phi"]
     o.step(4000)
     f = o.fields()
-    x = np.arange(nx)
     assert np.abs(f["phi"] - phi0).max() < 1e-2
-    assert np.abs(f["phi"] - mid).max() < 1e-4
-    c0 = (phi0[0] * x).sum() / phi0[0].sum()
-    assert (f["phi"][0] * x).sum() / f["phi"][0].sum() == pytest.approx(c0, abs=1e-6)
+    assert np.abs(f["phi"] - mid).max() < 3e-4
+    # the slab stays symmetric about its centre x = 32 (no drift)
+    row = f["phi"][0]
+    d = np.arange(1, 32)
+    assert np.abs(row[32 + d] - row[32 - d]).max() < 1e-9
     assert np.abs(f["ux"]).max() < 1e-6
     assert f["fs"].max() == 0.0
 
@@ -293,3 +297,21 @@ def test_final_height_of_frozen_column(oracle_mod):
     hf = ob["volume"] / p["ny"]
     assert hf == pytest.approx(H0 / sl, rel=0.01)
     assert ob["solid"] / p["ny"] == pytest.approx(H0 / sl, abs=1.0)
+
+
+def test_bulk_phase_field_stays_at_one_while_freezing(oracle_mod):
+    """Freezing with rho_s < rho_l injects volume at the front (Eqs. 19, 25-26)
+    while the flow answers through pressure waves. With the F_0 correction of
+    Eq. 36 taken as the non-equilibrium part of f_0 implied by Eq. 30,
+    (tau_f - 1/2) F_0, the order parameter inside the liquid and the solid
+    stays within a few 1e-3 of 1 and relaxes back; the printed tau F_0
+    lets it fall to ~0.8 at the wall over 2e4 steps."""
+    p, phi0, T0 = inputs.stefan()
+    o = run(oracle_mod, p, phi0, T0)
+    worst = []
+    for t in (300, 1000, 3000):
+        o.step(t - o.step_count)
+        ph = o.fields()["phi"][:, :110]
+        worst.append(np.abs(ph - 1.0).max())
+    assert max(worst) < 6e-3, worst
+    assert worst[-1] < 2e-3, worst
