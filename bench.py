@@ -42,6 +42,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=1024, help="lattice size of the bubble drop")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -281,9 +283,14 @@ def run_ours(args, dist: Dist):
     stream = lat.stream
     lat.init(phi0, T0)
 
-    # warm-up
+    # warm-up, including the library's autotuner (it advances the lattice with
+    # ordinary steps while it times each kernel layout)
+    tune = None
     if args.warmup:
         lat.step(args.warmup)
+    if not args.no_autotune:
+        tune = [float(t) for t in lat.autotune(steps=args.tune_steps)]
+    kernel = lat.kernel
     torch.cuda.synchronize()
     dist.barrier()
     torch.cuda.synchronize()
@@ -325,6 +332,7 @@ def run_ours(args, dist: Dist):
         ph.numpy()[:] = phi0
         tt.numpy()[:] = T0
         lat2 = lbm.Lattice([p], device=dev)
+        lat2.set_kernel(*kernel)
         torch.cuda.synchronize()
         dist.barrier()
         t0 = time.perf_counter()
@@ -363,6 +371,8 @@ def run_ours(args, dist: Dist):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
+            "kernel": {"kind": "strip" if kernel[0] == 1 else "tile", "params": list(kernel[1:]),
+                       "autotune_ms_per_step": tune},
             "clocks": clocks.summary(),
             "observables": {k: obs[k] for k in ("solid", "volume", "nonfinite")},
         }

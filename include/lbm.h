@@ -156,6 +156,37 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux);
 int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
                   const double* aux);
 
+/* Kernel layouts for lbm_step. Both compute the same arithmetic in the same
+   order, so they give bit-identical results.
+   LBM_KERNEL_TILE:  one CTA per tile of a x b sites with a shared-memory
+                     halo; handles every wall combination. (a, b) in
+                     {(32,8), (32,4), (64,4), (32,16)}; c ignored.
+   LBM_KERNEL_STRIP: one warp per strip of 30 columns x b rows (b >= 2) that
+                     keeps its halo in registers and warp shuffles; needs every
+                     lattice of the handle periodic in x. a = warps per CTA,
+                     c = register budget per thread: (a, c) in {(4,128),
+                     (4,168), (4,255), (8,128), (2,128)}.
+   lbm_create picks STRIP (4, 16, 168) when every lattice is periodic in x,
+   else TILE (32, 8). */
+#define LBM_KERNEL_TILE   0
+#define LBM_KERNEL_STRIP  1
+
+/* Select the kernel layout (host tables are rebuilt and uploaded on the
+   stream; synchronises it). LBM_EINVAL for an unsupported combination. */
+int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c);
+
+/* Current layout: out[0] = kind, out[1..3] = a, b, c as for lbm_set_kernel. */
+int lbm_get_kernel(const lbm_handle* h, int32_t* out);
+
+/* Autotuner: time every supported layout for this handle over `steps` time
+   steps each (after one warm-up step), measured with CUDA events on the
+   stream, and keep the fastest. The lattices are advanced by every step it
+   runs (lbm_step_count grows accordingly); all layouts compute identical
+   results, so the trajectory is the one lbm_step would have produced.
+   times_ms (may be NULL) receives up to `cap` mean step times in the order
+   the candidates were tried; *n_tried their number. Synchronises. */
+int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, int32_t* n_tried);
+
 /* Number of time steps taken since the last lbm_init_fields of instance 0. */
 int64_t lbm_step_count(const lbm_handle* h);
 

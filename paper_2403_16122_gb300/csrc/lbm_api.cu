@@ -13,6 +13,7 @@
 #include "lbm_internal.h"
 
 using lbmk::Inst;
+using lbmk::Item;
 using lbmk::Tile;
 
 namespace {
@@ -42,10 +43,10 @@ bool valid_params(const lbm_params& p) {
 int elem_size(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
 
 struct Layout {
-    uint64_t inst_off, tile_off, part_off, obs_off, stage_off;
+    uint64_t inst_off, tile_off, item_off, part_off, obs_off, stage_off;
     std::vector<uint64_t> pop_off[2], aux_off[2];
     uint64_t total;
-    int max_tiles, max_sites;
+    int max_tiles, max_items, max_parts, max_sites;
 };
 
 int max_tiles_of(const lbm_params& p) {
@@ -53,18 +54,27 @@ int max_tiles_of(const lbm_params& p) {
     return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
 }
 
+constexpr int kMinRows = 2;  // shortest strip segment
+int max_items_of(const lbm_params& p) {
+    return ((p.nx + lbmk::kStripW - 1) / lbmk::kStripW) * ((p.ny + kMinRows - 1) / kMinRows);
+}
+
 Layout make_layout(const lbm_params* p, int n, int storage) {
     Layout L;
     uint64_t off = 0;
     L.max_tiles = 0;
+    L.max_items = 0;
     L.max_sites = 0;
     for (int k = 0; k < n; ++k) {
         L.max_tiles += max_tiles_of(p[k]);
+        if (p[k].periodic_x) L.max_items += max_items_of(p[k]);
         L.max_sites = std::max(L.max_sites, p[k].nx * p[k].ny);
     }
+    L.max_parts = std::max(L.max_tiles, L.max_items);
     L.inst_off = off; off = align_up(off + sizeof(Inst) * (uint64_t)n);
     L.tile_off = off; off = align_up(off + sizeof(Tile) * (uint64_t)L.max_tiles);
-    L.part_off = off; off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)L.max_tiles);
+    L.item_off = off; off = align_up(off + sizeof(Item) * (uint64_t)std::max(L.max_items, 1));
+    L.part_off = off; off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)L.max_parts);
     L.obs_off = off;  off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)n);
     L.stage_off = off; off = align_up(off + sizeof(double) * 2 * (uint64_t)L.max_sites);
     for (int b = 0; b < 2; ++b) {
@@ -89,7 +99,11 @@ struct lbm_handle {
     std::vector<lbm_params> params;
     int n_inst = 0;
     int storage = 0;
-    int tx = 32, ty = 8;
+    int kind = LBM_KERNEL_TILE;
+    int tx = 32, ty = 8;                 // tile shape
+    int warps = 4, rows = 16, regs = 168; // strip layout
+    std::vector<Item> items;
+    Item* d_items = nullptr;
     cudaStream_t stream = nullptr;
     char* ws = nullptr;
     Layout layout;
@@ -180,12 +194,39 @@ void build_tiles(lbm_handle* h) {
     }
 }
 
+// Strip items ordered by (lattice, row segment, strip) so that warps that run
+// together touch neighbouring columns of the same rows.
+void build_items(lbm_handle* h) {
+    h->items.clear();
+    for (int k = 0; k < h->n_inst; ++k) {
+        const lbm_params& p = h->params[k];
+        h->inst[k].part_begin = (int)h->items.size();
+        for (int y0 = 0; y0 < p.ny; y0 += h->rows)
+            for (int x0 = 0; x0 < p.nx; x0 += lbmk::kStripW) {
+                Item it;
+                memset(&it, 0, sizeof(it));
+                it.inst = k;
+                it.x0 = x0;
+                it.y0 = y0;
+                it.y1 = std::min(y0 + h->rows, p.ny);
+                it.part = (int)h->items.size();
+                h->items.push_back(it);
+            }
+        h->inst[k].part_end = (int)h->items.size();
+    }
+}
+
 int upload_tables(lbm_handle* h) {
+    if (h->kind == LBM_KERNEL_STRIP) build_items(h); else build_tiles(h);
     cudaError_t e = cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(Inst) * h->n_inst,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = cudaMemcpyAsync(h->d_tiles, h->tiles.data(), sizeof(Tile) * h->tiles.size(),
-                        cudaMemcpyHostToDevice, h->stream);
+    if (h->kind == LBM_KERNEL_STRIP)
+        e = cudaMemcpyAsync(h->d_items, h->items.data(), sizeof(Item) * h->items.size(),
+                            cudaMemcpyHostToDevice, h->stream);
+    else
+        e = cudaMemcpyAsync(h->d_tiles, h->tiles.data(), sizeof(Tile) * h->tiles.size(),
+                            cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(h->stream);  // host tables may change after return
     return e == cudaSuccess ? LBM_OK : cuda_fail(e);
@@ -227,11 +268,14 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
     h->init_L.resize(n_inst);
     h->d_inst = reinterpret_cast<Inst*>(h->ws + h->layout.inst_off);
     h->d_tiles = reinterpret_cast<Tile*>(h->ws + h->layout.tile_off);
+    h->d_items = reinterpret_cast<Item*>(h->ws + h->layout.item_off);
     h->d_part = reinterpret_cast<double*>(h->ws + h->layout.part_off);
     h->d_obs = reinterpret_cast<double*>(h->ws + h->layout.obs_off);
     h->d_stage = reinterpret_cast<double*>(h->ws + h->layout.stage_off);
     for (int k = 0; k < n_inst; ++k) fill_inst(h, k);
-    build_tiles(h);
+    bool all_px = true;
+    for (int k = 0; k < n_inst; ++k) all_px = all_px && p[k].periodic_x;
+    h->kind = all_px ? LBM_KERNEL_STRIP : LBM_KERNEL_TILE;
     rc = upload_tables(h);
     if (rc != LBM_OK) {
         delete h;
@@ -276,8 +320,12 @@ int lbm_step(lbm_handle* h, int64_t n) {
     if (!h->initialised) return LBM_ESTATE;
     for (int64_t k = 0; k < n; ++k) {
         const int obs = (k == n - 1);
-        cudaError_t e = lbmk::launch_step(h->tx, h->ty, h->storage, h->d_inst, h->d_tiles,
-                                          (int)h->tiles.size(), h->parity, obs, h->d_part, h->stream);
+        cudaError_t e =
+            h->kind == LBM_KERNEL_STRIP
+                ? lbmk::launch_step_strip(h->warps, h->regs, h->d_inst, h->d_items,
+                                          (int)h->items.size(), h->parity, obs, h->d_part, h->stream)
+                : lbmk::launch_step(h->tx, h->ty, h->storage, h->d_inst, h->d_tiles,
+                                    (int)h->tiles.size(), h->parity, obs, h->d_part, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
         h->parity ^= 1;
@@ -362,6 +410,77 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double*
     h->initialised = true;
     h->have_obs = false;
     return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c) {
+    if (!h) return LBM_EINVAL;
+    if (kind == LBM_KERNEL_TILE) {
+        if (!lbmk::tile_supported(a, b)) return LBM_EINVAL;
+        h->kind = kind; h->tx = a; h->ty = b;
+    } else if (kind == LBM_KERNEL_STRIP) {
+        for (int k = 0; k < h->n_inst; ++k)
+            if (!h->params[k].periodic_x) return LBM_EINVAL;
+        if (!lbmk::strip_supported(a, c) || b < kMinRows) return LBM_EINVAL;
+        h->kind = kind; h->warps = a; h->rows = b; h->regs = c;
+    } else {
+        return LBM_EINVAL;
+    }
+    h->have_obs = false;  // partial slots are renumbered
+    return upload_tables(h);
+}
+
+int lbm_get_kernel(const lbm_handle* h, int32_t* out) {
+    if (!h || !out) return LBM_EINVAL;
+    out[0] = h->kind;
+    if (h->kind == LBM_KERNEL_STRIP) { out[1] = h->warps; out[2] = h->rows; out[3] = h->regs; }
+    else { out[1] = h->tx; out[2] = h->ty; out[3] = 0; }
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, int32_t* n_tried) {
+    if (!h || steps < 1) return LBM_EINVAL;
+    if (!h->initialised) return LBM_ESTATE;
+    struct Cand { int kind, a, b, c; };
+    std::vector<Cand> cands;
+    bool all_px = true;
+    for (int k = 0; k < h->n_inst; ++k) all_px = all_px && h->params[k].periodic_x;
+    if (all_px) {
+        const int rows[] = {8, 16, 32};
+        const int var[][2] = {{4, 168}, {4, 128}, {8, 128}, {4, 255}};
+        for (int r : rows)
+            for (auto& v : var) cands.push_back({LBM_KERNEL_STRIP, v[0], r, v[1]});
+    }
+    cands.push_back({LBM_KERNEL_TILE, 32, 8, 0});
+    cands.push_back({LBM_KERNEL_TILE, 64, 4, 0});
+    cands.push_back({LBM_KERNEL_TILE, 32, 16, 0});
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LBM_ECUDA; }
+    int best = -1, tried = 0;
+    float best_ms = 0.f;
+    int rc = LBM_OK;
+    for (size_t j = 0; j < cands.size() && rc == LBM_OK; ++j) {
+        const Cand& cd = cands[j];
+        if (lbm_set_kernel(h, cd.kind, cd.a, cd.b, cd.c) != LBM_OK) continue;
+        rc = lbm_step(h, 1);
+        if (rc != LBM_OK) break;
+        cudaEventRecord(e0, h->stream);
+        rc = lbm_step(h, steps);
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LBM_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)steps;
+        if (times_ms && tried < cap) times_ms[tried] = ms;
+        ++tried;
+        if (best < 0 || ms < best_ms) { best = (int)j; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_tried) *n_tried = tried;
+    if (rc != LBM_OK) return rc;
+    if (best < 0) return LBM_EINVAL;
+    return lbm_set_kernel(h, cands[best].kind, cands[best].a, cands[best].b, cands[best].c);
 }
 
 int64_t lbm_step_count(const lbm_handle* h) { return h ? h->steps : -1; }

@@ -47,6 +47,23 @@ struct Tile {
     int inst, x0, y0, tw, th, part;
 };
 
+// One warp's work in the strip kernel: lattice `inst`, output columns
+// [x0, x0 + 30) (a periodic x axis), rows [y0, y1), observable slot `part`.
+struct Item {
+    int inst, x0, y0, y1, part, pad[3];
+};
+
+// Output columns of one warp strip (the two remaining lanes hold the halo).
+constexpr int kStripW = 30;
+
+// Launch one time step over every strip item (one warp each, `warps` warps
+// per CTA) in stream s.
+cudaError_t launch_step_strip(int warps, int regs, const Inst* d_inst, const Item* d_items,
+                              int n_items, int parity, int obs, double* d_partials, cudaStream_t s);
+
+// Supported strip-kernel variants (warps per CTA, register budget).
+bool strip_supported(int warps, int regs);
+
 // Launch one time step over every tile (grid = n_tiles CTAs) in stream s.
 // parity selects the source buffer; obs != 0 also writes per-tile partials.
 cudaError_t launch_step(int tx, int ty, int storage, const Inst* d_inst,

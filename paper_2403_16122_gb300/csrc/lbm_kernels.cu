@@ -190,6 +190,157 @@ __device__ void block_reduce_obs(double v[kObs], double* __restrict__ out) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-site update shared by the tile and strip kernels
+// ---------------------------------------------------------------------------
+// Isotropic stencils of Eq. 38 at one site: gradients of phi, rho, p^{n-1},
+// S^{n-1} and the Laplacian of phi. Neighbours are accumulated in the order
+// i = 1..8 by every kernel (ghost values where a neighbour lies behind a
+// wall), then scaled by stencil_finish.
+struct Stencil {
+    float gphx, gphy, lph, grx, gry, gpx, gpy, gSx, gSy;
+};
+
+__device__ __forceinline__ void stencil_zero(Stencil& st) {
+    st.gphx = st.gphy = st.lph = st.grx = st.gry = st.gpx = st.gpy = st.gSx = st.gSy = 0.f;
+}
+
+template <int I>
+__device__ __forceinline__ void stencil_acc(Stencil& st, float phi0, float zp, float zr,
+                                            float zq, float zs) {
+    constexpr float w = WGT(I);
+    st.gphx += w * CX(I) * zp; st.gphy += w * CY(I) * zp;
+    st.lph += w * (zp - phi0);
+    st.grx += w * CX(I) * zr; st.gry += w * CY(I) * zr;
+    st.gpx += w * CX(I) * zq; st.gpy += w * CY(I) * zq;
+    st.gSx += w * CX(I) * zs; st.gSy += w * CY(I) * zs;
+}
+
+__device__ __forceinline__ void stencil_finish(Stencil& st) {
+    st.gphx *= 3.f; st.gphy *= 3.f; st.lph *= 6.f;
+    st.grx *= 3.f; st.gry *= 3.f; st.gpx *= 3.f; st.gpy *= 3.f; st.gSx *= 3.f; st.gSy *= 3.f;
+}
+
+// Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
+// three collisions (Eqs. 21, 25, 27-28, 30-33) and the store of the
+// post-collision populations and carried fields of one site. The order of
+// every floating-point operation is fixed here, so all kernels built on it
+// produce bit-identical results.
+template <bool OBS>
+__device__ __forceinline__ void site_update(const Phys& P, int flags, const Macro& m,
+                                            const float g[9], const float h[9], const float f[9],
+                                            float phiux_p, float phiuy_p, const Stencil& st,
+                                            float* __restrict__ B, float* __restrict__ Baux,
+                                            long long plane, int own, bool on_col, bool on_row,
+                                            double ob[kObs]) {
+    const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
+    const float gphx = st.gphx, gphy = st.gphy, lph = st.lph, grx = st.grx, gry = st.gry;
+    const float gpx = st.gpx, gpy = st.gpy, gSx = st.gSx, gSy = st.gSy;
+
+    // Eqs. 11-12 (phi_l = 1, phi_g = 0)
+    const float muphi = 4.f * P.beta * (phi - 1.f) * phi * (phi - 0.5f) - P.kappa * lph;
+    float Fx = muphi * gphx, Fy = muphi * gphy;
+    if (flags & kStMask) { Fx *= (1.f - fs); Fy *= (1.f - fs); }
+
+    // Eqs. 34-35: u* from the flow moments, solid forcing f = -f_s u*
+    float mx = 0.f, my = 0.f, fne0 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        mx += CX(i) * f[i];
+        my += CY(i) * f[i];
+        if (i) fne0 += f[i];
+    }
+    const float usx = (mx + 0.5f * Fx) / rho, usy = (my + 0.5f * Fy) / rho;
+    const float ffx = -fs * usx, ffy = -fs * usy;
+    const float ux = usx + 0.5f * ffx, uy = usy + 0.5f * ffy;
+    const float uu = ux * ux + uy * uy;
+
+    // Eq. 33 source terms (grad p, grad S lagged one step)
+    const float S = rho * mdot + ux * grx + uy * gry;
+    const float Ftx = Fx - gpx + (grx + gSx) * (1.f / 3.f);
+    const float Fty = Fy - gpy + (gry + gSy) * (1.f / 3.f);
+    const float uFt = ux * Ftx + uy * Fty;
+    const float mu = mix3(fs, phi, P.mu_s, P.mu_l, P.mu_g);
+    const float tau_f = mu / (rho * (1.f / 3.f)) + 0.5f;
+    const float omega_f = 1.f / tau_f;
+    const float Fpx = Fx + rho * ffx, Fpy = Fy + rho * ffy;  // F + rho f
+    const float F0 = kW0 * (S - 3.f * uFt);
+    // Eq. 36 with s_0(u) = -w_0 u.u / (2 c_s^2); the F_0 correction is the
+    // first-order non-equilibrium part of f_0 that Eq. 30 implies,
+    // (tau_f - 1/2) F_0
+    const float pn = (1.f / 3.f) / (1.f - kW0) *
+                     (fne0 + 0.5f * S + (tau_f - 0.5f) * F0 + rho * (-kW0 * 1.5f * uu));
+
+    // Phase field: n, lambda (Eq. 3), d_t(phi u) (Eq. 37), G_i (Eq. 25)
+    // regularised normal n = grad phi / sqrt(|grad phi|^2 + eps^2)
+    const float rn = rsqrtf(gphx * gphx + gphy * gphy + P.eps2);
+    const float nx_ = gphx * rn, ny_ = gphy * rn;
+    const float lam = P.lam_coef * phi * (1.f - phi);
+    const float phiux = phi * ux, phiuy = phi * uy;
+    const float ax = (phiux - phiux_p) + (1.f / 3.f) * lam * nx_;
+    const float ay = (phiuy - phiuy_p) + (1.f / 3.f) * lam * ny_;
+    const float gsrc = 1.f - 0.5f * P.omega_g;
+    const float pmd = phi * mdot;
+
+    // Enthalpy: T from Eq. 9b on the shifted enthalpy,
+    // H - H_s - L f_l = H' - H_s + L (f_l^{n-1} - f_l); inside the mushy
+    // range the exact value is T_m (evaluating the sum there would only
+    // add the rounding of f_l times L)
+    const float dL = P.L * (m.flp - m.fl);
+    const float T = m.mushy ? P.Tm : P.Tm + (m.Hp - P.Hs + dL) / P.Cp;
+
+    const float fsrc = 1.f - 0.5f * omega_f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float w = WGT(i);
+        const float cu = CX(i) * ux + CY(i) * uy;
+        // g (Eqs. 21, 24, 25)
+        const float geq = w * phi * (1.f + 3.f * cu);
+        const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
+        const float gn = g[i] - P.omega_g * (g[i] - geq) + gsrc * Gi;
+        // h (Eqs. 27-28); h_0 carried shifted by -L f_l
+        float hn;
+        if (i == 0) {
+            const float heq0 = m.Hp + dL - P.Cpref * T + kW0 * T * (P.Cpref - P.Cp * 1.5f * uu);
+            hn = (1.f - P.omega_h) * (h[0] + dL) + P.omega_h * heq0;
+        } else {
+            const float heq = w * T * (P.Cpref + P.Cp * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+            hn = h[i] - P.omega_h * (h[i] - heq);
+        }
+        // f (Eqs. 30-33)
+        const float si = w * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+        const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
+        const float cF = CX(i) * Ftx + CY(i) * Fty;
+        const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
+        const float fn = f[i] - omega_f * (f[i] - feq) + fsrc * Fi;
+        B[(long long)(i) * plane + own] = gn;
+        B[(long long)(9 + i) * plane + own] = hn;
+        B[(long long)(18 + i) * plane + own] = fn;
+    }
+    Baux[own] = m.fl;
+    Baux[plane + own] = phiux;
+    Baux[2 * plane + own] = phiuy;
+    Baux[3 * plane + own] = pn;
+    Baux[4 * plane + own] = S;
+
+    if (OBS) {
+        const double dphi = phi, dfs = fs;
+        ob[0] += dphi;
+        ob[1] += dfs;
+        ob[2] += (double)m.Hp + (double)P.L * (double)m.flp;
+        ob[3] += rho;
+        ob[4] += dfs * P.rho_s + (1.0 - dfs) * (double)clamp01(phi) * P.rho_l;
+        ob[5] += mdot;
+        ob[6] += dphi * (double)mdot;
+        ob[7] += on_col ? dfs : 0.0;
+        ob[8] += on_row ? dfs : 0.0;
+        ob[9] = fmax(ob[9], sqrt((double)uu));
+        const bool bad = !isfinite(phi) || !isfinite(m.Hp) || !isfinite(ux) || !isfinite(uy) ||
+                         !isfinite(pn);
+        ob[10] += bad ? 1.0 : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The fused step kernel
 // ---------------------------------------------------------------------------
 template <int TX, int TY, bool OBS>
@@ -362,131 +513,226 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
         for (int j = 0; j < kObs; ++j) ob[j] = 0.0;
     }
     if (active) {
-        const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
-        // Eq. 38 from shared memory: grad = 3 sum w c z, lap = 6 sum w (z - z0)
-        float gphx = 0.f, gphy = 0.f, lph = 0.f, grx = 0.f, gry = 0.f;
-        float gpx = 0.f, gpy = 0.f, gSx = 0.f, gSy = 0.f;
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const int s = SI(tx + CX(i), ty + CY(i));
-            const float w = WGT(i);
-            const float zp = s_phi[s], zr = s_rho[s], zq = s_p[s], zs = s_S[s];
-            gphx += w * CX(i) * zp; gphy += w * CY(i) * zp;
-            lph += w * (zp - phi);
-            grx += w * CX(i) * zr; gry += w * CY(i) * zr;
-            gpx += w * CX(i) * zq; gpy += w * CY(i) * zq;
-            gSx += w * CX(i) * zs; gSy += w * CY(i) * zs;
-        }
-        gphx *= 3.f; gphy *= 3.f; lph *= 6.f;
-        grx *= 3.f; gry *= 3.f; gpx *= 3.f; gpy *= 3.f; gSx *= 3.f; gSy *= 3.f;
-
-        // Eqs. 11-12 (phi_l = 1, phi_g = 0)
-        const float muphi = 4.f * P.beta * (phi - 1.f) * phi * (phi - 0.5f) - P.kappa * lph;
-        float Fx = muphi * gphx, Fy = muphi * gphy;
-        if (l.flags & kStMask) { Fx *= (1.f - fs); Fy *= (1.f - fs); }
-
-        // Eqs. 34-35: u* from the flow moments, solid forcing f = -f_s u*
-        float mx = 0.f, my = 0.f, fne0 = 0.f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            mx += CX(i) * f[i];
-            my += CY(i) * f[i];
-            if (i) fne0 += f[i];
-        }
-        const float usx = (mx + 0.5f * Fx) / rho, usy = (my + 0.5f * Fy) / rho;
-        const float ffx = -fs * usx, ffy = -fs * usy;
-        const float ux = usx + 0.5f * ffx, uy = usy + 0.5f * ffy;
-        const float uu = ux * ux + uy * uy;
-
-        // Eq. 33 source terms (grad p, grad S lagged one step)
-        const float S = rho * mdot + ux * grx + uy * gry;
-        const float Ftx = Fx - gpx + (grx + gSx) * (1.f / 3.f);
-        const float Fty = Fy - gpy + (gry + gSy) * (1.f / 3.f);
-        const float uFt = ux * Ftx + uy * Fty;
-        const float mu = mix3(fs, phi, P.mu_s, P.mu_l, P.mu_g);
-        const float tau_f = mu / (rho * (1.f / 3.f)) + 0.5f;
-        const float omega_f = 1.f / tau_f;
-        const float Fpx = Fx + rho * ffx, Fpy = Fy + rho * ffy;  // F + rho f
-        const float F0 = kW0 * (S - 3.f * uFt);
-        // Eq. 36 with s_0(u) = -w_0 u.u / (2 c_s^2); the F_0 correction is the
-        // first-order non-equilibrium part of f_0 that Eq. 30 implies,
-        // (tau_f - 1/2) F_0
-        const float pn = (1.f / 3.f) / (1.f - kW0) *
-                         (fne0 + 0.5f * S + (tau_f - 0.5f) * F0 + rho * (-kW0 * 1.5f * uu));
-
-        // Phase field: n, lambda (Eq. 3), d_t(phi u) (Eq. 37), G_i (Eq. 25)
-        // regularised normal n = grad phi / sqrt(|grad phi|^2 + eps^2)
-        const float rn = rsqrtf(gphx * gphx + gphy * gphy + P.eps2);
-        const float nx_ = gphx * rn, ny_ = gphy * rn;
-        const float lam = P.lam_coef * phi * (1.f - phi);
-        const float phiux = phi * ux, phiuy = phi * uy;
-        const float ax = (phiux - phiux_p) + (1.f / 3.f) * lam * nx_;
-        const float ay = (phiuy - phiuy_p) + (1.f / 3.f) * lam * ny_;
-        const float gsrc = 1.f - 0.5f * P.omega_g;
-        const float pmd = phi * mdot;
-
-        // Enthalpy: T from Eq. 9b on the shifted enthalpy,
-        // H - H_s - L f_l = H' - H_s + L (f_l^{n-1} - f_l); inside the mushy
-        // range the exact value is T_m (evaluating the sum there would only
-        // add the rounding of f_l times L)
-        const float dL = P.L * (m.flp - m.fl);
-        const float T = m.mushy ? P.Tm : P.Tm + (m.Hp - P.Hs + dL) / P.Cp;
-        const float cpT = P.Cp * T;
-
-        const int own = y * l.pitch + x;
-        const float fsrc = 1.f - 0.5f * omega_f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float w = WGT(i);
-            const float cu = CX(i) * ux + CY(i) * uy;
-            // g (Eqs. 21, 24, 25)
-            const float geq = w * phi * (1.f + 3.f * cu);
-            const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
-            const float gn = g[i] - P.omega_g * (g[i] - geq) + gsrc * Gi;
-            // h (Eqs. 27-28); h_0 carried shifted by -L f_l
-            float hn;
-            if (i == 0) {
-                const float heq0 = m.Hp + dL - P.Cpref * T + kW0 * T * (P.Cpref - P.Cp * 1.5f * uu);
-                hn = (1.f - P.omega_h) * (h[0] + dL) + P.omega_h * heq0;
-            } else {
-                const float heq = w * T * (P.Cpref + P.Cp * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
-                hn = h[i] - P.omega_h * (h[i] - heq);
-            }
-            // f (Eqs. 30-33)
-            const float si = w * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-            const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
-            const float cF = CX(i) * Ftx + CY(i) * Fty;
-            const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
-            const float fn = f[i] - omega_f * (f[i] - feq) + fsrc * Fi;
-            B[(long long)(i) * l.plane + own] = gn;
-            B[(long long)(9 + i) * l.plane + own] = hn;
-            B[(long long)(18 + i) * l.plane + own] = fn;
-        }
-        Baux[own] = m.fl;
-        Baux[l.plane + own] = phiux;
-        Baux[2 * l.plane + own] = phiuy;
-        Baux[3 * l.plane + own] = pn;
-        Baux[4 * l.plane + own] = S;
-        (void)cpT;
-
-        if (OBS) {
-            const double dphi = phi, dfs = fs;
-            ob[0] = dphi;
-            ob[1] = dfs;
-            ob[2] = (double)m.Hp + (double)P.L * (double)m.flp;
-            ob[3] = rho;
-            ob[4] = dfs * P.rho_s + (1.0 - dfs) * (double)clamp01(phi) * P.rho_l;
-            ob[5] = mdot;
-            ob[6] = dphi * (double)mdot;
-            ob[7] = (x == l.nx / 2) ? dfs : 0.0;
-            ob[8] = (y == l.ny / 2) ? dfs : 0.0;
-            ob[9] = sqrt((double)uu);
-            const bool bad = !isfinite(phi) || !isfinite(m.Hp) || !isfinite(ux) ||
-                             !isfinite(uy) || !isfinite(pn);
-            ob[10] = bad ? 1.0 : 0.0;
-        }
+        Stencil st;
+        stencil_zero(st);
+#define LBM_TILE_ACC(I)                                                                  \
+    {                                                                                    \
+        const int sidx = SI(tx + CX(I), ty + CY(I));                                     \
+        stencil_acc<I>(st, m.phi, s_phi[sidx], s_rho[sidx], s_p[sidx], s_S[sidx]);       \
+    }
+        LBM_TILE_ACC(1) LBM_TILE_ACC(2) LBM_TILE_ACC(3) LBM_TILE_ACC(4)
+        LBM_TILE_ACC(5) LBM_TILE_ACC(6) LBM_TILE_ACC(7) LBM_TILE_ACC(8)
+#undef LBM_TILE_ACC
+        stencil_finish(st);
+        site_update<OBS>(P, l.flags, m, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
+                         y * l.pitch + x, x == l.nx / 2, y == l.ny / 2, ob);
     }
     if (OBS) block_reduce_obs<NT>(ob, partials + (long long)T.part * kObs);
+}
+
+
+// ---------------------------------------------------------------------------
+// Warp-strip kernel (lattices periodic in x)
+// ---------------------------------------------------------------------------
+// One warp advances a strip of 30 output columns over rows [y0, y1). Lane l
+// holds column x0 - 1 + l, so lanes 0 and 31 are the halo of the strip and
+// neighbours along x come from warp shuffles. Along y the warp keeps phi,
+// rho, p^{n-1} and S^{n-1} of rows y-1, y and y+1 in registers and computes
+// the macroscopic fields one row ahead of the row it collides. No shared
+// memory and no block barrier are involved; the y halo costs two extra rows
+// of local macroscopic fields per strip.
+
+// Pull of set SET at (x, y) for a row whose sources do not cross a wall; the
+// column offsets xm/xp and row offsets rm/rp are already wrapped.
+template <int SET>
+__device__ __forceinline__ void pull_rows(const Lat& l, int xc, int xm, int xp, int r0,
+                                          int rm, int rp, float v[9]) {
+    const float* __restrict__ A = l.A + (long long)(9 * SET) * l.plane;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int r = CY(i) > 0 ? rm : (CY(i) < 0 ? rp : r0);   // source row y - cy
+        const int c = CX(i) > 0 ? xm : (CX(i) < 0 ? xp : xc);   // source column x - cx
+        v[i] = __ldg(A + (long long)i * l.plane + r + c);
+    }
+}
+
+struct RowCtx {
+    int xc, xm, xp;   // this lane's column and its periodic neighbours
+    bool py;          // periodic y
+};
+
+// Pulls and local macroscopic fields of lattice row y at this lane's column.
+template <int SET>
+__device__ __forceinline__ void pull_row(const Lat& l, const RowCtx& c, int y, float abb,
+                                         float v[9]) {
+    if (c.py || (y >= 1 && y <= l.ny - 2)) {
+        const int ym = y == 0 ? l.ny - 1 : y - 1;
+        const int yp = y == l.ny - 1 ? 0 : y + 1;
+        pull_rows<SET>(l, c.xc, c.xm, c.xp, y * l.pitch, ym * l.pitch, yp * l.pitch, v);
+    } else {
+        pull_set<SET>(l, c.xc, y, abb, v);
+    }
+}
+
+// Value of `v` at the lane c_x columns away (c_x in {-1, 0, 1}).
+__device__ __forceinline__ float lane_shift(float v, int cx) {
+    if (cx > 0) return __shfl_down_sync(0xffffffffu, v, 1);
+    if (cx < 0) return __shfl_up_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// Wetting ghost (Eqs. 39-41) for the row behind a wall: a is the adjacent
+// lattice row, b the next one; outer_a/outer_b hold phi one column beyond
+// the strip for the halo lanes.
+__device__ __forceinline__ float strip_wet_ghost(float a, float b, float outer_a, float outer_b,
+                                                 int lane, float tan_w) {
+    float ap = __shfl_down_sync(0xffffffffu, a, 1), am = __shfl_up_sync(0xffffffffu, a, 1);
+    float bp = __shfl_down_sync(0xffffffffu, b, 1), bm = __shfl_up_sync(0xffffffffu, b, 1);
+    if (lane == 31) { ap = outer_a; bp = outer_b; }
+    if (lane == 0) { am = outer_a; bm = outer_b; }
+    const float d0 = 0.5f * (ap - am);
+    const float d1 = 0.5f * (bp - bm);
+    return a + tan_w * fabsf(1.5f * d0 - 0.5f * d1);
+}
+
+template <int WARPS, int MINB, bool OBS>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
+           int parity, double* __restrict__ partials) {
+    const int lane = threadIdx.x & 31;
+    const int it = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (it >= n_items) return;  // whole warp leaves together; no block barrier below
+    const Item W = items[it];
+    const Inst& I = insts[W.inst];
+    const Phys P = load_phys(I);
+    Lat l;
+    l.A = static_cast<const float*>(I.pop[parity]);
+    l.Aaux = I.aux[parity];
+    l.plane = I.plane; l.nx = I.nx; l.ny = I.ny; l.pitch = I.pitch; l.flags = I.flags;
+    float* __restrict__ B = static_cast<float*>(I.pop[parity ^ 1]);
+    float* __restrict__ Baux = I.aux[parity ^ 1];
+    const float abb = P.Cpref * P.Tw;
+    const int nx = l.nx, ny = l.ny;
+
+    RowCtx c;
+    const int xl = W.x0 - 1 + lane;
+    c.xc = ((xl % nx) + nx) % nx;
+    c.xm = c.xc == 0 ? nx - 1 : c.xc - 1;
+    c.xp = c.xc == nx - 1 ? 0 : c.xc + 1;
+    c.py = (l.flags & kPeriodicY) != 0;
+    const bool out_lane = lane >= 1 && lane <= kStripW && xl < nx;
+    const bool halo_lane = lane == 0 || lane == 31;
+    const int x_outer = lane == 0 ? c.xm : c.xp;   // one column beyond the strip
+
+    // phi one column beyond the strip at the wall-adjacent rows (halo lanes)
+    float oB0 = 0.f, oB1 = 0.f, oT0 = 0.f, oT1 = 0.f;
+    auto outer_phi = [&](int y) {
+        float gg[9], hh[9];
+        pull_set<0>(l, x_outer, y, abb, gg);
+        pull_set<1>(l, x_outer, y, abb, hh);
+        return local_macro(P, gg, hh, ldAux(l, 0, y * l.pitch + x_outer)).phi;
+    };
+    auto note_outer = [&](int y) {
+        if (c.py || !halo_lane) return;
+        if (y == 0) oB0 = outer_phi(y);
+        if (y == 1) oB1 = outer_phi(y);
+        if (y == ny - 1) oT0 = outer_phi(y);
+        if (y == ny - 2) oT1 = outer_phi(y);
+    };
+    // local macroscopic fields of row y at this lane's column (the pulled g
+    // and h are dropped; the collision of the row pulls them again, from L1)
+    auto row_macro = [&](int y, Macro& m, float& p, float& S) {
+        float gg[9], hh[9];
+        pull_row<0>(l, c, y, abb, gg);
+        pull_row<1>(l, c, y, abb, hh);
+        const int idx = y * l.pitch + c.xc;
+        m = local_macro(P, gg, hh, ldAux(l, 0, idx));
+        p = ldAux(l, 3, idx);
+        S = ldAux(l, 4, idx);
+        note_outer(y);
+    };
+
+    double ob[kObs];
+    if (OBS) {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) ob[j] = 0.0;
+    }
+
+    // rows y-1 (m), y (0) and y+1 (p) of phi, rho, p^{n-1}, S^{n-1}
+    float phm = 0.f, ph0, php = 0.f, rhm = 0.f, rh0, rhp = 0.f;
+    float pm = 0.f, p0, pp = 0.f, Sm = 0.f, S0, Sp = 0.f;
+    Macro mO;
+    const int y0 = W.y0;
+    row_macro(y0, mO, p0, S0);
+    ph0 = mO.phi; rh0 = mO.rho;
+    if (y0 >= 1 || c.py) {
+        Macro mm;
+        row_macro(y0 == 0 ? ny - 1 : y0 - 1, mm, pm, Sm);
+        phm = mm.phi; rhm = mm.rho;
+    }
+
+    for (int y = y0; y < W.y1; ++y) {
+        Macro mN;
+        if (y + 1 < ny || c.py) {
+            row_macro(y + 1 == ny ? 0 : y + 1, mN, pp, Sp);
+            php = mN.phi; rhp = mN.rho;
+        } else {
+            // row ny lies behind the top wall: ghost from rows ny-1 and ny-2
+            php = strip_wet_ghost(ph0, phm, oT0, oT1, lane, P.tan_w);
+            rhp = rh0; pp = p0; Sp = S0;
+        }
+        if (y == 0 && !c.py) {
+            // row -1 lies behind the bottom wall: ghost from rows 0 and 1
+            phm = strip_wet_ghost(ph0, php, oB0, oB1, lane, P.tan_w);
+            rhm = rh0; pm = p0; Sm = S0;
+        }
+
+        Stencil st;
+        stencil_zero(st);
+#define LBM_STRIP_ACC(I)                                                                 \
+    {                                                                                    \
+        constexpr int cy = CY(I);                                                        \
+        const float vphi = cy > 0 ? php : (cy < 0 ? phm : ph0);                          \
+        const float vrho = cy > 0 ? rhp : (cy < 0 ? rhm : rh0);                          \
+        const float vp = cy > 0 ? pp : (cy < 0 ? pm : p0);                               \
+        const float vS = cy > 0 ? Sp : (cy < 0 ? Sm : S0);                               \
+        stencil_acc<I>(st, ph0, lane_shift(vphi, CX(I)), lane_shift(vrho, CX(I)),        \
+                       lane_shift(vp, CX(I)), lane_shift(vS, CX(I)));                    \
+    }
+        LBM_STRIP_ACC(1) LBM_STRIP_ACC(2) LBM_STRIP_ACC(3) LBM_STRIP_ACC(4)
+        LBM_STRIP_ACC(5) LBM_STRIP_ACC(6) LBM_STRIP_ACC(7) LBM_STRIP_ACC(8)
+#undef LBM_STRIP_ACC
+        stencil_finish(st);
+
+        if (out_lane) {
+            float g[9], h[9], f[9];
+            pull_row<0>(l, c, y, abb, g);
+            pull_row<1>(l, c, y, abb, h);
+            pull_row<2>(l, c, y, abb, f);
+            const int own = y * l.pitch + c.xc;
+            const float phiux_p = ldAux(l, 1, own), phiuy_p = ldAux(l, 2, own);
+            site_update<OBS>(P, l.flags, mO, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
+                             own, c.xc == nx / 2, y == ny / 2, ob);
+        }
+
+        // advance the window
+        phm = ph0; ph0 = php; rhm = rh0; rh0 = rhp;
+        pm = p0; p0 = pp; Sm = S0; S0 = Sp;
+        mO = mN;
+    }
+
+    if (OBS) {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) {
+            double v = ob[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double u = __shfl_xor_sync(0xffffffffu, v, o);
+                v = (j == 9) ? fmax(v, u) : v + u;
+            }
+            if (lane == 0) partials[(long long)W.part * kObs + j] = v;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -524,18 +770,38 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
     }
 }
 
-// Per-lattice reduction of tile partials in a fixed order (deterministic).
-__global__ void reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
-                           double* __restrict__ out) {
+// Per-lattice reduction of the per-tile (or per-strip) partials: thread t
+// sums partials t, t + 256, ... in order, then a fixed shared-memory tree
+// combines the 256 sums, so the result does not depend on scheduling.
+constexpr int kRedThreads = 256;
+__global__ void __launch_bounds__(kRedThreads)
+reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
+           double* __restrict__ out) {
+    __shared__ double red[kObs][kRedThreads];
     const Inst& I = insts[blockIdx.x];
-    const int j = threadIdx.x;
-    if (j >= kObs) return;
-    double acc = 0.0;
-    for (int p = I.part_begin; p < I.part_end; ++p) {
-        const double v = partials[(long long)p * kObs + j];
-        acc = (j == 9) ? fmax(acc, v) : acc + v;
+    const int t = threadIdx.x;
+    double acc[kObs];
+#pragma unroll
+    for (int j = 0; j < kObs; ++j) acc[j] = 0.0;
+    for (int p = I.part_begin + t; p < I.part_end; p += kRedThreads) {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) {
+            const double v = partials[(long long)p * kObs + j];
+            acc[j] = (j == 9) ? fmax(acc[j], v) : acc[j] + v;
+        }
     }
-    out[(long long)blockIdx.x * kObs + j] = acc;
+#pragma unroll
+    for (int j = 0; j < kObs; ++j) red[j][t] = acc[j];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (t < w) {
+#pragma unroll
+            for (int j = 0; j < kObs; ++j)
+                red[j][t] = (j == 9) ? fmax(red[j][t], red[j][t + w]) : red[j][t] + red[j][t + w];
+        }
+        __syncthreads();
+    }
+    if (t < kObs) out[(long long)blockIdx.x * kObs + t] = red[t][0];
 }
 
 template <int TX, int TY>
@@ -548,7 +814,38 @@ cudaError_t launch_tile(const Inst* d_inst, const Tile* d_tiles, int n_tiles, in
     return cudaGetLastError();
 }
 
+template <int WARPS, int MINB>
+cudaError_t launch_strip_w(const Inst* d_inst, const Item* d_items, int n_items, int parity,
+                           int obs, double* d_partials, cudaStream_t s) {
+    const int blocks = (n_items + WARPS - 1) / WARPS;
+    if (obs)
+        step_strip<WARPS, MINB, true><<<blocks, WARPS * 32, 0, s>>>(d_inst, d_items, n_items, parity,
+                                                                   d_partials);
+    else
+        step_strip<WARPS, MINB, false><<<blocks, WARPS * 32, 0, s>>>(d_inst, d_items, n_items, parity,
+                                                                    d_partials);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_step_strip(int warps, int regs, const Inst* d_inst, const Item* d_items,
+                              int n_items, int parity, int obs, double* d_partials, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    // regs: register budget per thread (128, 168 or 255) via the minimum
+    // number of resident CTAs requested from the compiler
+    if (warps == 4 && regs == 128) return launch_strip_w<4, 4>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 4 && regs == 168) return launch_strip_w<4, 3>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 4 && regs == 255) return launch_strip_w<4, 1>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 8 && regs == 128) return launch_strip_w<8, 2>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 2 && regs == 128) return launch_strip_w<2, 8>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    return cudaErrorInvalidValue;
+}
+
+bool strip_supported(int warps, int regs) {
+    return (warps == 4 && (regs == 128 || regs == 168 || regs == 255)) ||
+           (warps == 8 && regs == 128) || (warps == 2 && regs == 128);
+}
 
 bool tile_supported(int tx, int ty) {
     return (tx == 32 && ty == 8) || (tx == 32 && ty == 4) || (tx == 64 && ty == 4) ||
@@ -567,7 +864,7 @@ cudaError_t launch_step(int tx, int ty, int storage, const Inst* d_inst, const T
 
 cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partials,
                           double* d_obs, cudaStream_t s) {
-    reduce_obs<<<n_inst, 32, 0, s>>>(d_inst, d_partials, d_obs);
+    reduce_obs<<<n_inst, kRedThreads, 0, s>>>(d_inst, d_partials, d_obs);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,9 @@ SYMBOLS = (
     "lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_observables_all", "lbm_get_state", "lbm_set_state",
     "lbm_step_count", "lbm_launch_count", "lbm_destroy", "lbm_error_string",
+    "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune",
 )
+LBM_KERNEL_TILE, LBM_KERNEL_STRIP = 0, 1
 
 
 def load(path: str | None = None):
@@ -91,6 +93,12 @@ def load(path: str | None = None):
         lib.lbm_launch_count.restype = i64
         lib.lbm_destroy.argtypes = [vp]
         lib.lbm_destroy.restype = None
+        lib.lbm_set_kernel.argtypes = [vp, i32, i32, i32, i32]
+        lib.lbm_set_kernel.restype = ctypes.c_int
+        lib.lbm_get_kernel.argtypes = [vp, P(i32)]
+        lib.lbm_get_kernel.restype = ctypes.c_int
+        lib.lbm_autotune.argtypes = [vp, i32, dp, i32, P(i32)]
+        lib.lbm_autotune.restype = ctypes.c_int
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in ("lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
@@ -197,6 +205,29 @@ def lbm_destroy(h):
     load().lbm_destroy(h)
 
 
+def lbm_set_kernel(h, kind: int, a: int, b: int, c: int = 0):
+    rc = load().lbm_set_kernel(h, int(kind), int(a), int(b), int(c))
+    if rc:
+        raise LbmError(rc, "lbm_set_kernel")
+
+
+def lbm_autotune(h, steps: int, cap: int = 64):
+    times = np.zeros(cap)
+    n = ctypes.c_int32()
+    rc = load().lbm_autotune(h, int(steps), _dptr(times), int(cap), ctypes.byref(n))
+    if rc:
+        raise LbmError(rc, "lbm_autotune")
+    return times[: n.value].copy()
+
+
+def lbm_get_kernel(h):
+    out = (ctypes.c_int32 * 4)()
+    rc = load().lbm_get_kernel(h, out)
+    if rc:
+        raise LbmError(rc, "lbm_get_kernel")
+    return tuple(out[:])
+
+
 # ---- convenience owner --------------------------------------------------------
 
 class Lattice:
@@ -263,6 +294,17 @@ class Lattice:
     def set_state(self, pops, aux, inst: int = 0):
         lbm_set_state(self._h, inst, pops, aux)
         return self
+
+    def set_kernel(self, kind: int, a: int, b: int, c: int = 0):
+        lbm_set_kernel(self._h, kind, a, b, c)
+        return self
+
+    def autotune(self, steps: int = 20):
+        return lbm_autotune(self._h, steps)
+
+    @property
+    def kernel(self):
+        return lbm_get_kernel(self._h)
 
     @property
     def step_count(self) -> int:
