@@ -221,7 +221,7 @@ def test_strip_kernel_matches_tile_kernel(case):
         assert np.abs(got[1] - want[1]).max() <= 1e-6, v
         obs = lat.observables()
         for k in ("volume", "solid", "enthalpy"):
-            assert obs[k] == pytest.approx(want_obs[k], rel=1e-6, abs=1e-9), (v, k)
+            assert obs[k] == pytest.approx(want_obs[k], rel=1e-6, abs=1e-6), (v, k)
 
 
 def test_kernel_selection_and_autotune():
