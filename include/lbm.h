@@ -51,6 +51,8 @@ extern "C" {
 #define LBM_ETIMEOUT   -4  /* a device-side wait gave up (batched launches)  */
 #define LBM_EUNSTABLE  -5  /* non-finite fields found by the last reduction  */
 #define LBM_ESTATE     -6  /* call out of order (e.g. step before init)      */
+#define LBM_ETOOLARGE  -7  /* lattice exceeds the fixed scratch of           */
+                           /* lbm_step_noalloc                               */
 
 /* Storage format of the distribution sets in device memory. Arithmetic is
    FP32 in every format. */
@@ -193,6 +195,47 @@ int64_t lbm_step_count(const lbm_handle* h);
 /* Number of kernel launches the library queued since the handle was created
    (every kernel, including initialisation and reductions). */
 int64_t lbm_launch_count(const lbm_handle* h);
+
+/* ---------------------------------------------------------------------------
+   Allocation-free single step (the paper has no counterpart; this entry point
+   exists for callers of the library, not for the method).
+
+   Some callers cannot allocate device memory at all: code that runs while a
+   CUDA graph is being captured, plugins inside a host application that owns
+   every device allocation, or real-time loops that must never stall in the
+   allocator. lbm_create needs a caller-owned workspace for its tables and
+   scratch; this entry point needs none. It advances one lattice by one time
+   step from the caller's state buffers (in) to the caller's state buffers
+   (out) and writes the observables record of that step, and it calls no
+   cudaMalloc, cudaFree or other allocating routine.
+
+   Buffers (device, caller-owned, FP32, 16-byte aligned): pops_in/pops_out hold
+   27 planes of ny rows of `pitch` floats (pitch >= nx) in the order g_0..g_8,
+   h_0..h_8, f_0..f_8, with h_0 stored shifted by -L f_l (L = Cp (T_m - T_w) /
+   Ste, f_l the first aux plane of the same buffer); aux_in/aux_out hold the
+   five carried planes f_l, (phi u)_x, (phi u)_y, p, S with the same pitch.
+   This is exactly the layout of a handle's state buffers. in and out must not
+   overlap. d_obs receives LBM_OBS_COUNT doubles (device memory).
+
+   Scratch: the per-tile partial sums of the observables live in one array of
+   LBM_NOALLOC_MAX_TILES * LBM_OBS_COUNT doubles (720 KiB) that is part of the
+   library's device image: every GPU that loads the library holds it until the
+   process exits. A lattice may have at most LBM_NOALLOC_MAX_TILES tiles of
+   32 x 8 sites, i.e. ceil(nx/32) * ceil(ny/8) <= 8192 (for example 1024 x 2048);
+   larger lattices get LBM_ETOOLARGE. Every slot the reduction reads is
+   written earlier in the same call, so nothing needs clearing, but all calls
+   share the array: calls that overlap on the GPU (for example on two streams
+   at once) race on it and their observables are undefined.
+
+   Device: the current device of the calling thread. On the first call for a
+   device the library looks up the array's device address (no allocation)
+   and caches it; make that first call before any stream capture begins.
+   Works for every wall combination (tile kernel). Returns LBM_EINVAL for bad
+   parameters, pointers or pitch, LBM_ECUDA for launch errors. */
+#define LBM_NOALLOC_MAX_TILES 8192
+int lbm_step_noalloc(const lbm_params* p, const float* pops_in, const float* aux_in,
+                     float* pops_out, float* aux_out, int32_t pitch, double* d_obs,
+                     void* cuda_stream);
 
 /* Release the handle (host memory only; the workspace stays the caller's).
    Waits for queued work on the stream first. NULL is accepted. */

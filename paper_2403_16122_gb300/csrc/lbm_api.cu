@@ -22,7 +22,7 @@ constexpr int kTileMinSites = 32 * 4;  // smallest supported tile (sizes the par
 constexpr uint64_t kAlign = 256;
 
 uint64_t align_up(uint64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+int pitch_of(int nx) { return lbmk::pitch_for(nx); }
 
 bool valid_params(const lbm_params& p) {
     if (p.nx < 3 || p.ny < 3) return false;
@@ -131,45 +131,13 @@ int cuda_fail(cudaError_t e) {
 
 void fill_inst(lbm_handle* h, int k) {
     const lbm_params& p = h->params[k];
-    const double cs2 = 1.0 / 3.0;
     Inst I;
-    memset(&I, 0, sizeof(I));
-    I.nx = p.nx; I.ny = p.ny; I.pitch = pitch_of(p.nx);
-    I.flags = (p.periodic_x ? lbmk::kPeriodicX : 0) | (p.periodic_y ? lbmk::kPeriodicY : 0) |
-              (p.dirichlet_x_lo ? lbmk::kDirXlo : 0) | (p.dirichlet_x_hi ? lbmk::kDirXhi : 0) |
-              (p.dirichlet_y_lo ? lbmk::kDirYlo : 0) | (p.dirichlet_y_hi ? lbmk::kDirYhi : 0) |
-              (p.st_mask_liquid ? lbmk::kStMask : 0);
-    I.plane = (long long)I.pitch * p.ny;
+    double L = 0.0;
+    lbmk::inst_from_params(p, &I, &L);
     for (int b = 0; b < 2; ++b) {
         I.pop[b] = h->ws + h->layout.pop_off[b][k];
         I.aux[b] = reinterpret_cast<float*>(h->ws + h->layout.aux_off[b][k]);
     }
-    const double L = p.Cp * (p.T_m - p.T_w) / p.Ste;  // Eq. 42
-    const double tau_g = p.mobility / cs2 + 0.5;
-    const double rho_g = p.rho_l / p.rho_ratio_lg, rho_s = p.rho_l * p.rho_ratio_sl;
-    const double mu_l = p.rho_l * cs2 * (p.tau_f_liquid - 0.5);
-    const double pi = acos(-1.0);
-    I.L = (float)L;
-    I.Hs = (float)(p.Cp * p.T_m);
-    I.Tm = (float)p.T_m;
-    I.Cp = (float)p.Cp;
-    I.Cpref = (float)p.Cp_ref;
-    I.Tw = (float)p.T_w;
-    I.omega_g = (float)(1.0 / tau_g);
-    I.omega_h = (float)(1.0 / p.tau_h);
-    I.kappa = (float)(1.5 * p.sigma * p.W);
-    I.beta = (float)(12.0 * p.sigma / p.W);
-    I.lam_coef = (float)(4.0 / p.W);
-    I.rho_s = (float)rho_s;
-    I.rho_l = (float)p.rho_l;
-    I.rho_g = (float)rho_g;
-    I.mu_s = (float)(mu_l * p.rho_ratio_sl);
-    I.mu_l = (float)mu_l;
-    I.mu_g = (float)(mu_l / p.mu_ratio_lg);
-    I.mdot_coef = (float)(1.0 - rho_s / p.rho_l);
-    I.tan_w = (float)tan(pi / 2.0 - p.theta_deg * pi / 180.0);
-    I.inv_ramp = (float)(1.0 / p.pc_ramp);
-    I.normal_eps2 = (float)(p.normal_eps * p.normal_eps);
     h->inst[k] = I;
     h->init_L[k] = L;
 }
@@ -502,8 +470,55 @@ const char* lbm_error_string(int code) {
         case LBM_ETIMEOUT: return "device-side wait timed out";
         case LBM_EUNSTABLE: return "non-finite fields";
         case LBM_ESTATE: return "call out of order";
+        case LBM_ETOOLARGE: return "lattice exceeds the fixed scratch of lbm_step_noalloc";
         default: return "unknown error";
     }
 }
 
 }  // extern "C"
+
+namespace lbmk {
+
+void inst_from_params(const lbm_params& p, Inst* out, double* Lout) {
+    const double cs2 = 1.0 / 3.0;
+    Inst I;
+    memset(&I, 0, sizeof(I));
+    I.nx = p.nx; I.ny = p.ny; I.pitch = pitch_for(p.nx);
+    I.flags = (p.periodic_x ? kPeriodicX : 0) | (p.periodic_y ? kPeriodicY : 0) |
+              (p.dirichlet_x_lo ? kDirXlo : 0) | (p.dirichlet_x_hi ? kDirXhi : 0) |
+              (p.dirichlet_y_lo ? kDirYlo : 0) | (p.dirichlet_y_hi ? kDirYhi : 0) |
+              (p.st_mask_liquid ? kStMask : 0);
+    I.plane = (long long)I.pitch * p.ny;
+    const double L = p.Cp * (p.T_m - p.T_w) / p.Ste;  // Eq. 42
+    const double tau_g = p.mobility / cs2 + 0.5;
+    const double rho_g = p.rho_l / p.rho_ratio_lg, rho_s = p.rho_l * p.rho_ratio_sl;
+    const double mu_l = p.rho_l * cs2 * (p.tau_f_liquid - 0.5);
+    const double pi = acos(-1.0);
+    I.L = (float)L;
+    I.Hs = (float)(p.Cp * p.T_m);
+    I.Tm = (float)p.T_m;
+    I.Cp = (float)p.Cp;
+    I.Cpref = (float)p.Cp_ref;
+    I.Tw = (float)p.T_w;
+    I.omega_g = (float)(1.0 / tau_g);
+    I.omega_h = (float)(1.0 / p.tau_h);
+    I.kappa = (float)(1.5 * p.sigma * p.W);
+    I.beta = (float)(12.0 * p.sigma / p.W);
+    I.lam_coef = (float)(4.0 / p.W);
+    I.rho_s = (float)rho_s;
+    I.rho_l = (float)p.rho_l;
+    I.rho_g = (float)rho_g;
+    I.mu_s = (float)(mu_l * p.rho_ratio_sl);
+    I.mu_l = (float)mu_l;
+    I.mu_g = (float)(mu_l / p.mu_ratio_lg);
+    I.mdot_coef = (float)(1.0 - rho_s / p.rho_l);
+    I.tan_w = (float)tan(pi / 2.0 - p.theta_deg * pi / 180.0);
+    I.inv_ramp = (float)(1.0 / p.pc_ramp);
+    I.normal_eps2 = (float)(p.normal_eps * p.normal_eps);
+    *out = I;
+    *Lout = L;
+}
+
+bool params_valid(const lbm_params& p) { return valid_params(p); }
+
+}  // namespace lbmk

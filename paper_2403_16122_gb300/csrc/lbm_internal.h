@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "lbm.h"
+
 namespace lbmk {
 
 constexpr int kObs = 11;  // observables per instance (LBM_OBS_COUNT)
@@ -84,6 +86,24 @@ struct InitConst {
 cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage,
                         InitConst c, const double* d_phi0, const double* d_T0,
                         int parity, cudaStream_t s);
+
+// One time step of the 32 x 8 tile kernel for a single lattice whose record
+// is passed by value (no device tables), with the per-tile observable
+// partials in `scratch` (n_tiles * kObs doubles) and the reduced record in
+// d_obs (kObs doubles). Buffer 0 of I is the source, buffer 1 the target.
+cudaError_t launch_step_noalloc(const Inst& I, int tiles_x, int n_tiles, double* scratch,
+                                double* d_obs, cudaStream_t s);
+
+// Physics constants of a lattice record from its problem statement (the
+// pointers, pitch and observable slots are left to the caller); *L gets the
+// latent heat in double precision.
+void inst_from_params(const lbm_params& p, Inst* I, double* L);
+
+// Parameter checks of lbm_workspace_size / lbm_create.
+bool params_valid(const lbm_params& p);
+
+// Pitch (elements per row) the library uses for a lattice of width nx.
+inline int pitch_for(int nx) { return (nx + 31) / 32 * 32; }
 
 // Supported tile shapes (TX x TY threads, one site per thread).
 bool tile_supported(int tx, int ty);

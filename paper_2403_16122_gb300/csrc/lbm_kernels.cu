@@ -343,17 +343,15 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
 // ---------------------------------------------------------------------------
 // The fused step kernel
 // ---------------------------------------------------------------------------
+// One CTA advances tile T of lattice I (the body of every tile kernel).
 template <int TX, int TY, bool OBS>
-__global__ void __launch_bounds__(TX * TY)
-step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int parity,
-          double* __restrict__ partials) {
+__device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int parity,
+                                          double* __restrict__ partials) {
     constexpr int NT = TX * TY;
     constexpr int SW = TX + 4;                  // shared row width (2-cell halo)
     constexpr int SH = TY + 4;
     __shared__ float s_phi[SH * SW], s_rho[SH * SW], s_p[SH * SW], s_S[SH * SW];
 
-    const Tile T = tiles[blockIdx.x];
-    const Inst& I = insts[T.inst];
     const Phys P = load_phys(I);
     Lat l;
     l.A = static_cast<const float*>(I.pop[parity]);
@@ -528,6 +526,30 @@ step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int pa
                          y * l.pitch + x, x == l.nx / 2, y == l.ny / 2, ob);
     }
     if (OBS) block_reduce_obs<NT>(ob, partials + (long long)T.part * kObs);
+}
+
+template <int TX, int TY, bool OBS>
+__global__ void __launch_bounds__(TX * TY)
+step_fp32(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int parity,
+          double* __restrict__ partials) {
+    const Tile T = tiles[blockIdx.x];
+    tile_step<TX, TY, OBS>(insts[T.inst], T, parity, partials);
+}
+
+// Handle-free variant for lbm_step_noalloc: the lattice record arrives by
+// value, the 32 x 8 tile follows from the block index, and the per-tile
+// observable partials go to the caller-supplied scratch array.
+template <bool OBS>
+__global__ void __launch_bounds__(256)
+step_tile_noalloc(const Inst I, int tiles_x, double* __restrict__ partials) {
+    Tile T;
+    T.inst = 0;
+    T.x0 = (int)(blockIdx.x % tiles_x) * 32;
+    T.y0 = (int)(blockIdx.x / tiles_x) * 8;
+    T.tw = min(32, I.nx - T.x0);
+    T.th = min(8, I.ny - T.y0);
+    T.part = (int)blockIdx.x;
+    tile_step<32, 8, OBS>(I, T, 0, partials);
 }
 
 
@@ -774,16 +796,15 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
 // sums partials t, t + 256, ... in order, then a fixed shared-memory tree
 // combines the 256 sums, so the result does not depend on scheduling.
 constexpr int kRedThreads = 256;
-__global__ void __launch_bounds__(kRedThreads)
-reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
-           double* __restrict__ out) {
+__device__ __forceinline__ void reduce_range(int begin, int end,
+                                             const double* __restrict__ partials,
+                                             double* __restrict__ out) {
     __shared__ double red[kObs][kRedThreads];
-    const Inst& I = insts[blockIdx.x];
     const int t = threadIdx.x;
     double acc[kObs];
 #pragma unroll
     for (int j = 0; j < kObs; ++j) acc[j] = 0.0;
-    for (int p = I.part_begin + t; p < I.part_end; p += kRedThreads) {
+    for (int p = begin + t; p < end; p += kRedThreads) {
 #pragma unroll
         for (int j = 0; j < kObs; ++j) {
             const double v = partials[(long long)p * kObs + j];
@@ -801,7 +822,19 @@ reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
         }
         __syncthreads();
     }
-    if (t < kObs) out[(long long)blockIdx.x * kObs + t] = red[t][0];
+    if (t < kObs) out[t] = red[t][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
+           double* __restrict__ out) {
+    const Inst& I = insts[blockIdx.x];
+    reduce_range(I.part_begin, I.part_end, partials, out + (long long)blockIdx.x * kObs);
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_noalloc(int n_parts, const double* __restrict__ partials, double* __restrict__ out) {
+    reduce_range(0, n_parts, partials, out);
 }
 
 template <int TX, int TY>
@@ -860,6 +893,15 @@ cudaError_t launch_step(int tx, int ty, int storage, const Inst* d_inst, const T
     if (tx == 64 && ty == 4) return launch_tile<64, 4>(d_inst, d_tiles, n_tiles, parity, obs, d_partials, s);
     if (tx == 32 && ty == 16) return launch_tile<32, 16>(d_inst, d_tiles, n_tiles, parity, obs, d_partials, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_noalloc(const Inst& I, int tiles_x, int n_tiles, double* scratch,
+                                double* d_obs, cudaStream_t s) {
+    step_tile_noalloc<true><<<n_tiles, 256, 0, s>>>(I, tiles_x, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_noalloc<<<1, kRedThreads, 0, s>>>(n_tiles, scratch, d_obs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partials,

@@ -19,6 +19,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_build", "liblbmfreeze.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LBM_ETOOLARGE = -7
+LBM_NOALLOC_MAX_TILES = 8192
 LBM_STORE_FP32, LBM_STORE_FP16, LBM_STORE_BF16 = 0, 1, 2
 OBS_NAMES = (
     "volume", "solid", "enthalpy", "mass", "condensed_mass", "mdot",
@@ -60,7 +62,7 @@ SYMBOLS = (
     "lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_observables_all", "lbm_get_state", "lbm_set_state",
     "lbm_step_count", "lbm_launch_count", "lbm_destroy", "lbm_error_string",
-    "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune",
+    "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune", "lbm_step_noalloc",
 )
 LBM_KERNEL_TILE, LBM_KERNEL_STRIP = 0, 1
 
@@ -99,6 +101,8 @@ def load(path: str | None = None):
         lib.lbm_get_kernel.restype = ctypes.c_int
         lib.lbm_autotune.argtypes = [vp, i32, dp, i32, P(i32)]
         lib.lbm_autotune.restype = ctypes.c_int
+        lib.lbm_step_noalloc.argtypes = [P(lbm_params), vp, vp, vp, vp, i32, vp, vp]
+        lib.lbm_step_noalloc.restype = ctypes.c_int
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in ("lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
@@ -209,6 +213,18 @@ def lbm_set_kernel(h, kind: int, a: int, b: int, c: int = 0):
     rc = load().lbm_set_kernel(h, int(kind), int(a), int(b), int(c))
     if rc:
         raise LbmError(rc, "lbm_set_kernel")
+
+
+def lbm_step_noalloc(cfg: dict, pops_in: int, aux_in: int, pops_out: int, aux_out: int,
+                     pitch: int, d_obs: int, stream: int):
+    """One time step of one lattice on caller-owned device buffers (integer
+    device addresses), with no handle and no device allocation."""
+    p = make_params(cfg)
+    rc = load().lbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(pops_in), ctypes.c_void_p(aux_in),
+                                 ctypes.c_void_p(pops_out), ctypes.c_void_p(aux_out), int(pitch),
+                                 ctypes.c_void_p(d_obs), ctypes.c_void_p(stream))
+    if rc:
+        raise LbmError(rc, "lbm_step_noalloc")
 
 
 def lbm_autotune(h, steps: int, cap: int = 64):
