@@ -31,6 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "MLUPS (all 3 populations) & % HBM peak; FP16-store/batched vs plain FP32"
 BYTES_PER_LU_FP32 = 256  # 27 populations + 5 carried fields, read + write, FP32
+BYTES_PER_LU_FP16 = 176  # 24 16-bit populations + 10 FP32 planes (5 carried, phi/T refs, 3 rest pops), read + write
 WORKLOAD = "bubble_drop_1024x1024_fp32"
 
 
@@ -44,6 +45,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-steps", type=int, default=10)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP16-storage comparison on the same workload")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched forms (256-lattice sweep, 1024-lattice FP16 batch)")
+    ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -348,6 +354,38 @@ def run_ours(args, dist: Dist):
                        "lbm_observables (device-to-host read, synchronising)"}
         lat2.close()
 
+    # the FP16-storage form on the same workload and GPU (FP32 arithmetic)
+    forms = None
+    if not args.no_forms:
+        forms = {}
+        lat16 = lbm.Lattice([p], storage=lbm.LBM_STORE_FP16, device=dev)
+        lat16.init(phi0, T0)
+        lat16.step(max(args.warmup, 3))
+        if not args.no_autotune:
+            lat16.autotune(steps=args.tune_steps)
+        k16 = max(1, min(args.steps, 3000))
+        torch.cuda.synchronize()
+        s16 = torch.cuda.Event(enable_timing=True)
+        e16 = torch.cuda.Event(enable_timing=True)
+        s16.record(lat16.stream)
+        lat16.step(k16)
+        e16.record(lat16.stream)
+        e16.synchronize()
+        ms16 = s16.elapsed_time(e16) / k16
+        ob16 = lat16.observables(check=False)
+        forms["fp16_storage"] = {
+            "value": sites / (ms16 * 1e-3) / 1e6, "unit": "MLUPS", "steps": k16,
+            "ms_per_step": ms16, "bytes_per_lu": BYTES_PER_LU_FP16,
+            "hbm_frac": BYTES_PER_LU_FP16 * sites / (ms16 * 1e-3) / 1e9 / peak,
+            "speedup_vs_fp32": ms_per_step / ms16,
+            "kernel": list(lat16.kernel),
+            "observables_after_warmup_and_steps": {k: ob16[k] for k in ("solid", "volume")},
+        }
+        lat16.close()
+
+    if forms is not None and not args.no_batched:
+        forms.update(batched_forms(args, dev, peak))
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -368,6 +406,7 @@ def run_ours(args, dist: Dist):
                        "l2": "inputs larger than L2 (268 MB moved per step)",
                        "bytes_per_lu": BYTES_PER_LU_FP32},
             "roofline": roofline,
+            "forms": forms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -379,6 +418,126 @@ def run_ours(args, dist: Dist):
         print(json.dumps(line), flush=True)
     lat.close()
     return 0
+
+
+def _timed_steps(lat, k):
+    """Mean ms per step of k steps of handle `lat`, CUDA events on its stream."""
+    import torch
+
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(lat.stream)
+    lat.step(k)
+    e.record(lat.stream)
+    e.synchronize()
+    return s.elapsed_time(e) / k
+
+
+def _batch_handle(cases, storage, dev, exec_mode, chunk, tune_steps):
+    from paper_2403_16122_gb300 import lbm
+
+    lat = lbm.Lattice([c[0] for c in cases], storage=storage, device=dev)
+    for k, (_, phi0, T0) in enumerate(cases):
+        lat.init(phi0, T0, inst=k)
+    lat.step(3)
+    if tune_steps:
+        lat.autotune(steps=tune_steps)
+    lat.set_exec(exec_mode, chunk)
+    lat.step(chunk + 1)  # captures the graph of the chosen layout
+    # start the timed run from step 0, so that forms compare at equal steps
+    for k, (_, phi0, T0) in enumerate(cases):
+        lat.init(phi0, T0, inst=k)
+    return lat
+
+
+def batched_forms(args, dev, peak):
+    """The batched forms on the same GPU: (1) 256 sessile drops of uneven
+    size (grids 128..512 squared) in one handle, persistent launch replayed
+    from a CUDA graph, against the same drops advanced one lattice per launch;
+    (2) 1024 drops with 0-4 bubbles (grids 64..256 per side) in FP16 storage
+    against the same batch in FP32, both persistent."""
+    import numpy as np
+
+    from paper_2403_16122_gb300 import inputs, lbm
+
+    out = {}
+    k = max(8, args.batched_steps)
+    chunk = 64
+    tune = 0 if args.no_autotune else 4
+
+    sweep = inputs.batched_sweep(256)
+    sites = sum(p["nx"] * p["ny"] for p, _, _ in sweep)
+    lat = _batch_handle(sweep, lbm.LBM_STORE_FP32, dev, lbm.LBM_EXEC_PERSISTENT, chunk, tune)
+    ms_b = _timed_steps(lat, k)
+    ex, kern = lat.exec, lat.kernel
+    ob = lat.observables_all(check=False)
+    lat.close()
+    # the same lattices, one handle and one launch per lattice and step
+    singles = []
+    for c in sweep:
+        h = lbm.Lattice([c[0]], device=dev)
+        h.init(c[1], c[2]).step(3)
+        singles.append(h)
+    k1 = max(4, k // 10)
+    per = []
+    import torch
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    stream = singles[0].stream
+    t0.record(stream)
+    for h in singles:  # one lattice after the other
+        h.step(k1)
+    t1.record(stream)
+    t1.synchronize()
+    ms_p = t0.elapsed_time(t1) / k1
+    for h in singles:  # each lattice's own step time when run by itself
+        per.append(_timed_steps(h, 8))
+        h.close()
+    per = np.array(per)
+    out["batched_fp32_sweep256"] = {
+        "value": sites / (ms_b * 1e-3) / 1e6, "unit": "MLUPS", "instances": len(sweep),
+        "sites": sites, "steps": k, "ms_per_step": ms_b,
+        "hbm_frac": BYTES_PER_LU_FP32 * sites / (ms_b * 1e-3) / 1e9 / peak,
+        "exec": {"mode": "persistent+graph", "chunk": ex[1], "ctas": ex[2]},
+        "kernel": list(kern),
+        "unbatched": {"value": sites / (ms_p * 1e-3) / 1e6, "unit": "MLUPS", "steps": k1,
+                      "ms_per_step": ms_p, "what": "one handle per lattice, advanced one lattice after the other, one launch per step"},
+        "speedup_vs_unbatched": ms_p / ms_b,
+        "instance_ms_per_step": {"batched_all": ms_b,
+                                 "alone_p50": float(np.percentile(per, 50)),
+                                 "alone_p99": float(np.percentile(per, 99))},
+        "nonfinite": float(ob[:, lbm.OBS_NAMES.index("nonfinite")].sum()),
+    }
+
+    mixed = inputs.batched_bubbles(1024)
+    sites = sum(p["nx"] * p["ny"] for p, _, _ in mixed)
+    res = {}
+    for name, st in (("fp32", lbm.LBM_STORE_FP32), ("fp16", lbm.LBM_STORE_FP16)):
+        lat = _batch_handle(mixed, st, dev, lbm.LBM_EXEC_PERSISTENT, chunk, tune)
+        ms = _timed_steps(lat, k)
+        res[name] = (ms, lat.exec, lat.kernel, lat.observables_all(check=False))
+        lat.close()
+    ms32, ms16 = res["fp32"][0], res["fp16"][0]
+    i_s, i_v = lbm.OBS_NAMES.index("solid"), lbm.OBS_NAMES.index("volume")
+    o32, o16 = res["fp32"][3], res["fp16"][3]
+    out["batched_fp16_bubbles1024"] = {
+        "value": sites / (ms16 * 1e-3) / 1e6, "unit": "MLUPS", "instances": len(mixed),
+        "sites": sites, "steps": k, "ms_per_step": ms16,
+        "hbm_frac": BYTES_PER_LU_FP16 * sites / (ms16 * 1e-3) / 1e9 / peak,
+        "fp32_batched": {"value": sites / (ms32 * 1e-3) / 1e6, "ms_per_step": ms32,
+                         "hbm_frac": BYTES_PER_LU_FP32 * sites / (ms32 * 1e-3) / 1e9 / peak,
+                         "kernel": list(res["fp32"][2])},
+        "speedup_vs_fp32_batched": ms32 / ms16,
+        "exec": {"mode": "persistent+graph", "chunk": res["fp16"][1][1], "ctas": res["fp16"][1][2]},
+        "kernel": list(res["fp16"][2]),
+        "max_rel_diff_vs_fp32": {
+            "volume": float(np.max(np.abs(o16[:, i_v] - o32[:, i_v]) / np.abs(o32[:, i_v]))),
+            "solid": float(np.max(np.abs(o16[:, i_s] - o32[:, i_s]) / np.maximum(o32[:, i_s], 1.0))),
+        },
+    }
+    return out
 
 
 def main(argv=None):

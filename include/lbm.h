@@ -55,9 +55,22 @@ extern "C" {
                            /* lbm_step_noalloc                               */
 
 /* Storage format of the distribution sets in device memory. Arithmetic is
-   FP32 in every format. */
+   FP32 in every format.
+   LBM_STORE_FP32: 27 FP32 planes (h_0 shifted by -L f_l) + 5 FP32 carried
+                   planes: 256 bytes moved per lattice update.
+   LBM_STORE_FP16: the 24 moving populations as 16-bit deviations from a
+                   rest equilibrium: of the site they stream into for g and h
+                   (w_i phi, w_i Cp_ref T), of their source site's pressure
+                   for f (scaled by 2^12). The three rest populations stay
+                   FP32 and absorb the rounding errors of the site's moving
+                   ones, so the phi, H and f sums a site sends out are kept
+                   exactly. phi and T of each site are two more FP32 planes:
+                   176 bytes per lattice update. Needs every lattice periodic
+                   in x (strip layout). lbm_get_state / lbm_set_state convert
+                   to and from the same double layouts as FP32.
+   LBM_STORE_BF16: reserved (LBM_EINVAL). */
 #define LBM_STORE_FP32  0
-#define LBM_STORE_FP16  1  /* deviations from the local rest equilibrium    */
+#define LBM_STORE_FP16  1
 #define LBM_STORE_BF16  2
 
 /* Problem statement of one lattice (Sections 4.1-4.3). */
@@ -188,6 +201,47 @@ int lbm_get_kernel(const lbm_handle* h, int32_t* out);
    times_ms (may be NULL) receives up to `cap` mean step times in the order
    the candidates were tried; *n_tried their number. Synchronises. */
 int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, int32_t* n_tried);
+
+/* Execution form of lbm_step (no counterpart in the paper, which specifies
+   the update of Section 3, not how it is scheduled). Every form runs the
+   same step arithmetic; the last step of each lbm_step call is always one
+   ordinary launch that also writes the observable partials.
+   LBM_EXEC_LAUNCH:     one kernel launch per step (the default).
+   LBM_EXEC_GRAPH:      runs of `chunk` steps replay a CUDA graph of `chunk`
+                        step launches, captured on first use (one graph per
+                        starting buffer) on a private stream and launched on
+                        the handle's stream.
+   LBM_EXEC_PERSISTENT: runs of `chunk` steps replay a CUDA graph holding one
+                        cooperative persistent launch: a co-resident grid
+                        (lbm_get_exec out[2] CTAs) walks every strip item of
+                        every lattice, with a device-wide barrier between
+                        steps. Strip layout only. A barrier wait is bounded
+                        (2 s); one that runs out makes the kernel return and
+                        the next synchronising call (lbm_observables*) return
+                        LBM_ETIMEOUT, after which lbm_step refuses with
+                        LBM_ETIMEOUT until lbm_init_fields gives a new state.
+   Step results of LAUNCH and GRAPH are bitwise identical; PERSISTENT agrees
+   with them to FP32 rounding (a separately compiled kernel). */
+#define LBM_EXEC_LAUNCH      0
+#define LBM_EXEC_GRAPH       1
+#define LBM_EXEC_PERSISTENT  2
+
+/* Select the execution form; chunk in [1, 65536] steps. Captured graphs are
+   dropped (also by lbm_set_kernel, whose tables they use). LBM_EINVAL for an
+   unknown mode or chunk, or PERSISTENT with the tile layout (and
+   lbm_set_kernel refuses the tile layout while PERSISTENT is selected). */
+int lbm_set_exec(lbm_handle* h, int32_t mode, int32_t chunk);
+
+/* out[0] = mode, out[1] = chunk, out[2] = CTAs of one persistent launch for
+   the current layout (0 for the tile layout). */
+int lbm_get_exec(const lbm_handle* h, int32_t* out);
+
+/* Self-test of the bounded device-wide barrier: one CTA waits at a barrier
+   that no other CTA joins, gives up after limit_ns (0 < limit_ns <= 2e9),
+   raises its error word and returns. *err_flag receives that word (1 when
+   the expiry was reported). The handle's own state is untouched.
+   Synchronises. */
+int lbm_barrier_selftest(lbm_handle* h, uint64_t limit_ns, int32_t* err_flag);
 
 /* Number of time steps taken since the last lbm_init_fields of instance 0. */
 int64_t lbm_step_count(const lbm_handle* h);

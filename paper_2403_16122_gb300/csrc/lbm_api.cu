@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "lbm.h"
 #include "lbm_internal.h"
 
@@ -20,6 +22,16 @@ namespace {
 
 constexpr int kTileMinSites = 32 * 4;  // smallest supported tile (sizes the partials)
 constexpr uint64_t kAlign = 256;
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // device-wide barrier wait
+constexpr int kMaxChunk = 1 << 16;
+
+// Device-side synchronisation words of a handle (in the workspace).
+struct SyncBlock {
+    unsigned bar;        // barrier counter of the persistent kernel
+    int err;             // raised by a barrier wait that ran out
+    unsigned probe_bar;  // the barrier self-test's own pair
+    int probe_err;
+};
 
 uint64_t align_up(uint64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 int pitch_of(int nx) { return lbmk::pitch_for(nx); }
@@ -41,9 +53,29 @@ bool valid_params(const lbm_params& p) {
 }
 
 int elem_size(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
+// carried FP32 planes: f_l, (phi u)_x, (phi u)_y, p, S; for FP16 storage also
+// phi_ref, T_ref and the FP32 rest populations g_0, h_0 (shifted), f_0
+int aux_planes(int storage) { return storage == LBM_STORE_FP32 ? 5 : 10; }
+
+// D2Q9 directions and weights of the host-side state conversion (Eqs. 22-23)
+const int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+const int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+const float kWf[9] = {0x1.c71c72p-2f, 0x1.c71c72p-4f, 0x1.c71c72p-4f, 0x1.c71c72p-4f,
+                      0x1.c71c72p-4f, 0x1.c71c70p-6f, 0x1.c71c70p-6f, 0x1.c71c70p-6f,
+                      0x1.c71c70p-6f};
+
+// Site a population of (x, y) streams into along c_i (the site itself when
+// the link ends behind a wall).
+size_t dest_site(const lbm_params& p, int x, int y, int i) {
+    int xd = x + kCx[i], yd = y + kCy[i];
+    bool wall = false;
+    if (xd < 0 || xd >= p.nx) { if (p.periodic_x) xd = (xd + p.nx) % p.nx; else wall = true; }
+    if (yd < 0 || yd >= p.ny) { if (p.periodic_y) yd = (yd + p.ny) % p.ny; else wall = true; }
+    return wall ? (size_t)y * p.nx + x : (size_t)yd * p.nx + xd;
+}
 
 struct Layout {
-    uint64_t inst_off, tile_off, item_off, part_off, obs_off, stage_off;
+    uint64_t inst_off, tile_off, item_off, part_off, obs_off, stage_off, sync_off;
     std::vector<uint64_t> pop_off[2], aux_off[2];
     uint64_t total;
     int max_tiles, max_items, max_parts, max_sites;
@@ -77,6 +109,7 @@ Layout make_layout(const lbm_params* p, int n, int storage) {
     L.part_off = off; off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)L.max_parts);
     L.obs_off = off;  off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)n);
     L.stage_off = off; off = align_up(off + sizeof(double) * 2 * (uint64_t)L.max_sites);
+    L.sync_off = off; off = align_up(off + sizeof(SyncBlock));
     for (int b = 0; b < 2; ++b) {
         L.pop_off[b].resize(n);
         L.aux_off[b].resize(n);
@@ -85,7 +118,7 @@ Layout make_layout(const lbm_params* p, int n, int storage) {
         const uint64_t plane = (uint64_t)pitch_of(p[k].nx) * p[k].ny;
         for (int b = 0; b < 2; ++b) {
             L.pop_off[b][k] = off; off = align_up(off + plane * 27 * elem_size(storage));
-            L.aux_off[b][k] = off; off = align_up(off + plane * 5 * sizeof(float));
+            L.aux_off[b][k] = off; off = align_up(off + plane * aux_planes(storage) * sizeof(float));
         }
     }
     L.total = off;
@@ -120,6 +153,15 @@ struct lbm_handle {
     bool initialised = false;
     bool have_obs = false;
     std::vector<double> init_L;  // double L per instance (state conversion)
+    // execution form of lbm_step
+    int exec = LBM_EXEC_LAUNCH;
+    int chunk = 64;
+    int persist_grid = 0;              // CTAs of one persistent launch
+    SyncBlock* d_sync = nullptr;
+    bool persist_pending = false;      // a persistent launch ran since the last check
+    bool failed = false;               // a barrier wait ran out: state is not usable
+    cudaStream_t cap_stream = nullptr; // private stream for graph capture
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // `chunk` steps from parity 0 / 1
 };
 
 namespace {
@@ -184,7 +226,15 @@ void build_items(lbm_handle* h) {
     }
 }
 
+void drop_graphs(lbm_handle* h) {
+    for (auto& g : h->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
 int upload_tables(lbm_handle* h) {
+    drop_graphs(h);  // captured launches carry the old item counts
     if (h->kind == LBM_KERNEL_STRIP) build_items(h); else build_tiles(h);
     cudaError_t e = cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(Inst) * h->n_inst,
                                     cudaMemcpyHostToDevice, h->stream);
@@ -197,10 +247,78 @@ int upload_tables(lbm_handle* h) {
                             cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(h->stream);  // host tables may change after return
-    return e == cudaSuccess ? LBM_OK : cuda_fail(e);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->persist_grid = h->kind == LBM_KERNEL_STRIP
+                          ? lbmk::persistent_grid(h->warps, h->regs, h->storage, (int)h->items.size())
+                          : 0;
+    return LBM_OK;
+}
+
+// One time step through the ordinary kernels (obs != 0: with observable partials).
+cudaError_t enqueue_step(lbm_handle* h, int parity, int obs, cudaStream_t s) {
+    return h->kind == LBM_KERNEL_STRIP
+               ? lbmk::launch_step_strip(h->warps, h->regs, h->storage, h->d_inst, h->d_items,
+                                         (int)h->items.size(), parity, obs, h->d_part, s)
+               : lbmk::launch_step(h->tx, h->ty, h->storage, h->d_inst, h->d_tiles,
+                                   (int)h->tiles.size(), parity, obs, h->d_part, s);
+}
+
+// n steps without observables from `parity` as one persistent launch.
+cudaError_t enqueue_persistent(lbm_handle* h, int parity, int n, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&h->d_sync->bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return lbmk::launch_step_strip_persistent(h->warps, h->regs, h->storage, h->persist_grid,
+                                              h->d_inst, h->d_items, (int)h->items.size(),
+                                              parity, n, &h->d_sync->bar, &h->d_sync->err,
+                                              kBarrierLimitNs, s);
+}
+
+// Capture `chunk` steps from `parity` (one launch per step, or one persistent
+// launch) into an executable graph on the handle's private stream.
+int capture_chunk(lbm_handle* h, int parity, cudaGraphExec_t* out) {
+    if (!h->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { h->cap_stream = nullptr; return cuda_fail(e); }
+    }
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaError_t ee = cudaSuccess;
+    if (h->exec == LBM_EXEC_PERSISTENT) {
+        ee = enqueue_persistent(h, parity, h->chunk, h->cap_stream);
+    } else {
+        for (int k = 0; k < h->chunk && ee == cudaSuccess; ++k)
+            ee = enqueue_step(h, parity ^ (k & 1), 0, h->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);  // always ends the capture
+    if (ee == cudaSuccess) ee = e;
+    if (ee == cudaSuccess) ee = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return ee == cudaSuccess ? LBM_OK : cuda_fail(ee);
+}
+
+// Launches of our kernels that one enqueued unit of n steps amounts to.
+int64_t kernels_per(const lbm_handle* h, int64_t n) {
+    return h->exec == LBM_EXEC_PERSISTENT ? 1 : n;
 }
 
 bool inst_ok(const lbm_handle* h, int32_t inst) { return h && inst >= 0 && inst < h->n_inst; }
+
+// Synchronise the handle's stream; after persistent launches also read the
+// barrier error word (h->failed is raised when a wait ran out).
+cudaError_t sync_checked(lbm_handle* h) {
+    static thread_local int err_host = 0;
+    cudaError_t e = cudaSuccess;
+    const bool check = h->persist_pending;
+    if (check) e = cudaMemcpyAsync(&err_host, &h->d_sync->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    if (check) {
+        h->persist_pending = false;
+        if (err_host != 0) h->failed = true;
+    }
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -208,9 +326,12 @@ extern "C" {
 
 int lbm_workspace_size(const lbm_params* p, int32_t n_inst, int32_t storage, uint64_t* bytes) {
     if (!p || !bytes || n_inst < 1) return LBM_EINVAL;
-    if (storage != LBM_STORE_FP32) return LBM_EINVAL;
-    for (int k = 0; k < n_inst; ++k)
+    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return LBM_EINVAL;
+    for (int k = 0; k < n_inst; ++k) {
         if (!valid_params(p[k])) return LBM_EINVAL;
+        // 16-bit storage runs in the strip layout, which needs periodic x
+        if (storage == LBM_STORE_FP16 && !p[k].periodic_x) return LBM_EINVAL;
+    }
     *bytes = make_layout(p, n_inst, storage).total;
     return LBM_OK;
 }
@@ -240,6 +361,11 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
     h->d_part = reinterpret_cast<double*>(h->ws + h->layout.part_off);
     h->d_obs = reinterpret_cast<double*>(h->ws + h->layout.obs_off);
     h->d_stage = reinterpret_cast<double*>(h->ws + h->layout.stage_off);
+    h->d_sync = reinterpret_cast<SyncBlock*>(h->ws + h->layout.sync_off);
+    if (cudaMemsetAsync(h->d_sync, 0, sizeof(SyncBlock), h->stream) != cudaSuccess) {
+        delete h;
+        return LBM_ECUDA;
+    }
     for (int k = 0; k < n_inst; ++k) fill_inst(h, k);
     bool all_px = true;
     for (int k = 0; k < n_inst; ++k) all_px = all_px && p[k].periodic_x;
@@ -280,20 +406,49 @@ int lbm_init_fields(lbm_handle* h, int32_t inst, const double* phi0, const doubl
     h->initialised = true;
     h->have_obs = false;
     if (inst == 0) h->steps = 0;
+    if (h->failed) {  // a fresh state clears an expired barrier wait
+        e = cudaMemsetAsync(&h->d_sync->err, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->failed = false;
+    }
     return LBM_OK;
 }
 
 int lbm_step(lbm_handle* h, int64_t n) {
     if (!h || n < 0) return LBM_EINVAL;
     if (!h->initialised) return LBM_ESTATE;
-    for (int64_t k = 0; k < n; ++k) {
-        const int obs = (k == n - 1);
-        cudaError_t e =
-            h->kind == LBM_KERNEL_STRIP
-                ? lbmk::launch_step_strip(h->warps, h->regs, h->d_inst, h->d_items,
-                                          (int)h->items.size(), h->parity, obs, h->d_part, h->stream)
-                : lbmk::launch_step(h->tx, h->ty, h->storage, h->d_inst, h->d_tiles,
-                                    (int)h->tiles.size(), h->parity, obs, h->d_part, h->stream);
+    if (h->failed) return LBM_ETIMEOUT;
+    // every step but the last runs without observables, in the handle's form
+    int64_t body = n > 0 ? n - 1 : 0;
+    if (h->exec != LBM_EXEC_LAUNCH) {
+        while (body >= h->chunk) {
+            cudaGraphExec_t& g = h->graph[h->parity];
+            if (!g) {
+                const int rc = capture_chunk(h, h->parity, &g);
+                if (rc != LBM_OK) return rc;
+            }
+            cudaError_t e = cudaGraphLaunch(g, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+            h->launches += kernels_per(h, h->chunk);
+            h->persist_pending |= h->exec == LBM_EXEC_PERSISTENT;
+            h->parity ^= h->chunk & 1;
+            h->steps += h->chunk;
+            body -= h->chunk;
+        }
+        if (body > 0 && h->exec == LBM_EXEC_PERSISTENT) {
+            cudaError_t e = enqueue_persistent(h, h->parity, (int)body, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+            h->launches += 1;
+            h->persist_pending = true;
+            h->parity ^= (int)(body & 1);
+            h->steps += body;
+            body = 0;
+        }
+    }
+    for (int64_t k = 0; k < body + (n > 0 ? 1 : 0); ++k) {
+        const int obs = (k == body);
+        cudaError_t e = enqueue_step(h, h->parity, obs, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
         h->parity ^= 1;
@@ -313,8 +468,9 @@ int lbm_observables_all(lbm_handle* h, double* out) {
     if (!h->have_obs) return LBM_ESTATE;
     cudaError_t e = cudaMemcpyAsync(out, h->d_obs, sizeof(double) * lbmk::kObs * h->n_inst,
                                     cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = sync_checked(h);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (h->failed) return LBM_ETIMEOUT;
     for (int k = 0; k < h->n_inst; ++k)
         if (out[k * lbmk::kObs + LBM_OBS_NONFINITE] > 0) return LBM_EUNSTABLE;
     return LBM_OK;
@@ -325,14 +481,113 @@ int lbm_observables(lbm_handle* h, int32_t inst, double* out) {
     if (!h->have_obs) return LBM_ESTATE;
     cudaError_t e = cudaMemcpyAsync(out, h->d_obs + (size_t)inst * lbmk::kObs,
                                     sizeof(double) * lbmk::kObs, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = sync_checked(h);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (h->failed) return LBM_ETIMEOUT;
     return out[LBM_OBS_NONFINITE] > 0 ? LBM_EUNSTABLE : LBM_OK;
 }
+
+namespace {
+
+// FP16 storage: download, then decode every population with the references of
+// the site it streams into (the same arithmetic as the kernels' decode).
+int get_state_fp16(lbm_handle* h, int32_t inst, double* pops, double* aux) {
+    const lbm_params& p = h->params[inst];
+    const Inst& I = h->inst[inst];
+    const size_t n = (size_t)p.nx * p.ny;
+    std::vector<__half> tp((size_t)27 * n);
+    std::vector<float> ta((size_t)10 * n);
+    cudaError_t e = cudaMemcpy2DAsync(tp.data(), p.nx * sizeof(__half), I.pop[h->parity],
+                                      I.pitch * sizeof(__half), p.nx * sizeof(__half),
+                                      (size_t)27 * p.ny, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(ta.data(), p.nx * sizeof(float), I.aux[h->parity],
+                              I.pitch * sizeof(float), p.nx * sizeof(float), (size_t)10 * p.ny,
+                              cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const double L = h->init_L[inst];
+    const float* phr = ta.data() + 5 * n;
+    const float* Tr = ta.data() + 6 * n;
+    if (pops) {
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x) {
+                const size_t k = (size_t)y * p.nx + x;
+                pops[k] = ta[7 * n + k];                                   // g_0
+                pops[9 * n + k] = (double)ta[8 * n + k] + L * (double)ta[k]; // h_0 + L f_l
+                pops[18 * n + k] = ta[9 * n + k];                           // f_0
+                for (int i = 1; i < 9; ++i) {
+                    const size_t kd = dest_site(p, x, y, i);
+                    const float rg = __half2float(tp[i * n + k]);
+                    const float rh = __half2float(tp[(9 + i) * n + k]);
+                    const float rf = __half2float(tp[(18 + i) * n + k]);
+                    pops[i * n + k] = rg + kWf[i] * phr[kd];
+                    pops[(9 + i) * n + k] = rh + kWf[i] * I.Cpref * Tr[kd];
+                    pops[(18 + i) * n + k] = rf * (1.f / 4096.f) + kWf[i] * 3.f * ta[3 * n + k];
+                }
+            }
+    }
+    if (aux)
+        for (size_t k = 0; k < (size_t)5 * n; ++k) aux[k] = ta[k];
+    return LBM_OK;
+}
+
+// FP16 storage: choose the references of every site from the given state
+// (phi_ref = sum g, T_ref from Eq. 9 on sum h), then encode.
+int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
+    const lbm_params& p = h->params[inst];
+    const Inst& I = h->inst[inst];
+    const size_t n = (size_t)p.nx * p.ny;
+    const double L = h->init_L[inst];
+    std::vector<float> ta((size_t)10 * n);
+    for (size_t k = 0; k < (size_t)5 * n; ++k) ta[k] = (float)aux[k];
+    float* phr = ta.data() + 5 * n;
+    float* Tr = ta.data() + 6 * n;
+    const double Hs = p.Cp * p.T_m;
+    for (size_t k = 0; k < n; ++k) {
+        double phi = 0.0, H = 0.0;
+        for (int i = 0; i < 9; ++i) { phi += pops[i * n + k]; H += pops[(9 + i) * n + k]; }
+        double fl = (H - Hs) / L;
+        fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
+        phr[k] = (float)phi;
+        Tr[k] = (float)(p.T_m + (H - Hs - L * fl) / p.Cp);
+    }
+    std::vector<__half> tp((size_t)27 * n);
+    for (int y = 0; y < p.ny; ++y)
+        for (int x = 0; x < p.nx; ++x) {
+            const size_t k = (size_t)y * p.nx + x;
+            ta[7 * n + k] = (float)pops[k];
+            ta[8 * n + k] = (float)(pops[9 * n + k] - L * (double)ta[k]);
+            ta[9 * n + k] = (float)pops[18 * n + k];
+            for (int i = 1; i < 9; ++i) {
+                const size_t kd = dest_site(p, x, y, i);
+                tp[i * n + k] = __double2half(pops[i * n + k] - (double)(kWf[i] * phr[kd]));
+                tp[(9 + i) * n + k] =
+                    __double2half(pops[(9 + i) * n + k] - (double)(kWf[i] * I.Cpref * Tr[kd]));
+                const double fr = (double)(kWf[i] * 3.f * ta[3 * n + k]);
+                tp[(18 + i) * n + k] = __double2half((pops[(18 + i) * n + k] - fr) * 4096.0);
+            }
+        }
+    cudaError_t e = cudaMemcpy2DAsync(I.pop[h->parity], I.pitch * sizeof(__half), tp.data(),
+                                      p.nx * sizeof(__half), p.nx * sizeof(__half),
+                                      (size_t)27 * p.ny, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(I.aux[h->parity], I.pitch * sizeof(float), ta.data(),
+                              p.nx * sizeof(float), p.nx * sizeof(float), (size_t)10 * p.ny,
+                              cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->initialised = true;
+    h->have_obs = false;
+    return LBM_OK;
+}
+
+}  // namespace
 
 int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     if (!inst_ok(h, inst)) return LBM_EINVAL;
     if (!h->initialised) return LBM_ESTATE;
+    if (h->storage == LBM_STORE_FP16) return get_state_fp16(h, inst, pops, aux);
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
@@ -358,6 +613,7 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
 
 int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
     if (!inst_ok(h, inst) || !pops || !aux) return LBM_EINVAL;
+    if (h->storage == LBM_STORE_FP16) return set_state_fp16(h, inst, pops, aux);
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
@@ -383,7 +639,8 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double*
 int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c) {
     if (!h) return LBM_EINVAL;
     if (kind == LBM_KERNEL_TILE) {
-        if (!lbmk::tile_supported(a, b)) return LBM_EINVAL;
+        if (!lbmk::tile_supported(a, b) || h->storage != LBM_STORE_FP32) return LBM_EINVAL;
+        if (h->exec == LBM_EXEC_PERSISTENT) return LBM_EINVAL;  // persistent form is strip-only
         h->kind = kind; h->tx = a; h->ty = b;
     } else if (kind == LBM_KERNEL_STRIP) {
         for (int k = 0; k < h->n_inst; ++k)
@@ -395,6 +652,42 @@ int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c)
     }
     h->have_obs = false;  // partial slots are renumbered
     return upload_tables(h);
+}
+
+int lbm_set_exec(lbm_handle* h, int32_t mode, int32_t chunk) {
+    if (!h || chunk < 1 || chunk > kMaxChunk) return LBM_EINVAL;
+    if (mode != LBM_EXEC_LAUNCH && mode != LBM_EXEC_GRAPH && mode != LBM_EXEC_PERSISTENT)
+        return LBM_EINVAL;
+    if (mode == LBM_EXEC_PERSISTENT && (h->kind != LBM_KERNEL_STRIP || h->persist_grid <= 0))
+        return LBM_EINVAL;
+    drop_graphs(h);
+    h->exec = mode;
+    h->chunk = chunk;
+    return LBM_OK;
+}
+
+int lbm_get_exec(const lbm_handle* h, int32_t* out) {
+    if (!h || !out) return LBM_EINVAL;
+    out[0] = h->exec;
+    out[1] = h->chunk;
+    out[2] = h->persist_grid;
+    return LBM_OK;
+}
+
+int lbm_barrier_selftest(lbm_handle* h, uint64_t limit_ns, int32_t* err_flag) {
+    if (!h || !err_flag || limit_ns == 0 || limit_ns > kBarrierLimitNs) return LBM_EINVAL;
+    static thread_local int v = 0;
+    cudaError_t e = cudaMemsetAsync(&h->d_sync->probe_bar, 0, 2 * sizeof(int), h->stream);
+    if (e == cudaSuccess)
+        e = lbmk::launch_barrier_timeout_probe(&h->d_sync->probe_bar, &h->d_sync->probe_err,
+                                               limit_ns, h->stream);
+    h->launches++;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&v, &h->d_sync->probe_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *err_flag = v;
+    return LBM_OK;
 }
 
 int lbm_get_kernel(const lbm_handle* h, int32_t* out) {
@@ -418,9 +711,11 @@ int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, in
         for (int r : rows)
             for (auto& v : var) cands.push_back({LBM_KERNEL_STRIP, v[0], r, v[1]});
     }
-    cands.push_back({LBM_KERNEL_TILE, 32, 8, 0});
-    cands.push_back({LBM_KERNEL_TILE, 64, 4, 0});
-    cands.push_back({LBM_KERNEL_TILE, 32, 16, 0});
+    if (h->exec != LBM_EXEC_PERSISTENT) {  // the persistent form is strip-only
+        cands.push_back({LBM_KERNEL_TILE, 32, 8, 0});
+        cands.push_back({LBM_KERNEL_TILE, 64, 4, 0});
+        cands.push_back({LBM_KERNEL_TILE, 32, 16, 0});
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LBM_ECUDA; }
@@ -458,6 +753,8 @@ int64_t lbm_launch_count(const lbm_handle* h) { return h ? h->launches : -1; }
 void lbm_destroy(lbm_handle* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
@@ -515,6 +812,8 @@ void inst_from_params(const lbm_params& p, Inst* out, double* Lout) {
     I.tan_w = (float)tan(pi / 2.0 - p.theta_deg * pi / 180.0);
     I.inv_ramp = (float)(1.0 / p.pc_ramp);
     I.normal_eps2 = (float)(p.normal_eps * p.normal_eps);
+    I.inv_L = (float)(1.0 / L);
+    I.inv_Cp = (float)(1.0 / p.Cp);
     *out = I;
     *Lout = L;
 }

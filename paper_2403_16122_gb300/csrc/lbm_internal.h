@@ -40,7 +40,7 @@ struct Inst {
     float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef;
     float tan_w, inv_ramp;
     float normal_eps2;               // squared regularisation of the normal
-    float pad[2];
+    float inv_L, inv_Cp;
 };
 
 // One CTA's tile: lattice `inst`, origin (x0, y0), extent tw x th, and the
@@ -60,11 +60,31 @@ constexpr int kStripW = 30;
 
 // Launch one time step over every strip item (one warp each, `warps` warps
 // per CTA) in stream s.
-cudaError_t launch_step_strip(int warps, int regs, const Inst* d_inst, const Item* d_items,
-                              int n_items, int parity, int obs, double* d_partials, cudaStream_t s);
+cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_inst,
+                              const Item* d_items, int n_items, int parity, int obs,
+                              double* d_partials, cudaStream_t s);
 
 // Supported strip-kernel variants (warps per CTA, register budget).
 bool strip_supported(int warps, int regs);
+
+// Persistent form of the strip step: grid size (CTAs) of one cooperative
+// launch over n_items items, at most what the device holds resident at once;
+// 0 if the variant is unsupported.
+int persistent_grid(int warps, int regs, int storage, int n_items);
+
+// One cooperative launch of `grid` CTAs that advances every item by nsteps
+// steps (no observables) starting from buffer parity0, with a device-wide
+// barrier between steps on *d_bar (must be zero at launch; the caller resets
+// it in the same stream). A barrier wait longer than limit_ns sets *d_err.
+cudaError_t launch_step_strip_persistent(int warps, int regs, int storage, int grid,
+                                         const Inst* d_inst, const Item* d_items, int n_items,
+                                         int parity0, int nsteps, unsigned* d_bar, int* d_err,
+                                         unsigned long long limit_ns, cudaStream_t s);
+
+// One CTA waiting at a barrier that nobody else joins: sets *d_err once
+// limit_ns has passed, then returns.
+cudaError_t launch_barrier_timeout_probe(unsigned* d_bar, int* d_err,
+                                         unsigned long long limit_ns, cudaStream_t s);
 
 // Launch one time step over every tile (grid = n_tiles CTAs) in stream s.
 // parity selects the source buffer; obs != 0 also writes per-tile partials.

@@ -22,6 +22,8 @@
 //            populations and carried fields to the other buffer.
 // Time levels match the CPU reference: grad p and grad S use the previous
 // step's p and S; d_t(phi u) is a backward difference (Eq. 37).
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -65,18 +67,80 @@ __device__ __forceinline__ float mix3(float fs, float phi, float zs, float zl, f
 // ---------------------------------------------------------------------------
 // Storage access (FP32)
 // ---------------------------------------------------------------------------
-struct Lat {
+// NC selects the load path: true for kernels that run one step per launch
+// (the read-only, non-coherent path), false for the persistent kernel, where
+// a buffer read in one step was written by other CTAs in the previous step of
+// the same launch, so its loads bypass L1 and are served by the coherent L2.
+template <bool NC>
+struct LatT {
     const float* __restrict__ A;  // source populations (27 planes)
     const float* __restrict__ Aaux;
-    long long plane;
+    int plane;                    // elements per plane (27 planes fit 32-bit offsets)
     int nx, ny, pitch, flags;
 };
+using Lat = LatT<true>;
 
-__device__ __forceinline__ float ldA(const Lat& l, int plane, int idx) {
-    return __ldg(l.A + (long long)plane * l.plane + idx);
+template <bool NC>
+__device__ __forceinline__ float ld_f32(const float* p) {
+    if constexpr (NC) return __ldg(p); else return __ldcg(p);
 }
-__device__ __forceinline__ float ldAux(const Lat& l, int k, int idx) {
-    return __ldg(l.Aaux + (long long)k * l.plane + idx);
+template <bool NC>
+__device__ __forceinline__ float ld_f16(const __half* p) {
+    if constexpr (NC) return __half2float(__ldg(p)); else return __half2float(__ldcg(p));
+}
+
+// FP16 storage: population i of a set is stored as a 16-bit deviation from a
+// rest-equilibrium reference. For g and h the reference is taken at the site
+// the population is pulled into (the destination of its streaming link, or
+// the site itself for links that bounce at a wall): w_i phi for g, w_i Cp_ref
+// T for h_1..8 and the rest equilibrium of h_0 (kept in the shifted form of
+// the FP32 layout); the destination decodes with its own phi_ref and T_ref,
+// two FP32 planes written by the previous step. For f the reference is the
+// rest equilibrium at the pressure of the source site, p w_i / c_s^2
+// (p (w_0 - 1) / c_s^2 for i = 0), and the deviation is scaled by 2^12; the
+// destination reads the source pressures from the carried p plane it loads
+// for the pressure gradient anyway. The rest populations g_0, h_0 (shifted)
+// and f_0 stay in FP32 (carried planes 7, 8, 9) and absorb the rounding
+// errors of the site's eight 16-bit outgoing populations, so the zeroth
+// moment a site sends out (phi, H, and the f sum) is exact: rounding only
+// displaces a little of it along one link, which cancels between
+// neighbouring sites in smooth fields instead of accumulating.
+constexpr float kFScale = 4096.f, kInvFScale = 1.f / 4096.f;
+struct Ref {
+    float phi, T;
+};
+
+template <typename ST, bool NC>
+__device__ __forceinline__ float ldPop(const LatT<NC>& l, int plane, int idx) {
+    if constexpr (sizeof(ST) == 4) {
+        return ld_f32<NC>(l.A + (plane * l.plane + idx));
+    } else {
+        if (plane % 9 == 0) return ld_f32<NC>(l.Aaux + ((7 + plane / 9) * l.plane + idx));  // FP32 rest
+        const __half* A = reinterpret_cast<const __half*>(l.A);
+        return ld_f16<NC>(A + (plane * l.plane + idx));
+    }
+}
+
+// Stored value -> population (h_0 in the shifted form) for site reference r.
+template <typename ST, int SET>
+__device__ __forceinline__ float decode(int i, float raw, const Ref& r, float Cpref, float h0ref) {
+    if constexpr (sizeof(ST) == 4) {
+        return raw;
+    } else {
+        if (i == 0) return raw;  // rest populations are stored in FP32
+        if (SET == 0) return raw + WGT(i) * r.phi;
+        if (SET == 1) return i == 0 ? raw + r.T * h0ref : raw + WGT(i) * Cpref * r.T;
+        return raw * kInvFScale;  // the caller adds the source-pressure reference
+    }
+}
+
+// Rest equilibrium of f at pressure p (Eq. 31 with u = 0).
+__device__ __forceinline__ float f_rest(int i, float p) {
+    return (i == 0 ? (kW0 - 1.f) : WGT(i)) * 3.f * p;
+}
+template <bool NC>
+__device__ __forceinline__ float ldAux(const LatT<NC>& l, int k, int idx) {
+    return ld_f32<NC>(l.Aaux + (k * l.plane + idx));
 }
 
 // Pull of set `set` (0 g, 1 h, 2 f) at lattice site (x, y): v[i] is the
@@ -84,10 +148,13 @@ __device__ __forceinline__ float ldAux(const Lat& l, int k, int idx) {
 // half-way bounce-back of the site's own opposite population; for h at a
 // Dirichlet wall by anti-bounce-back -h + 2 w_i Cp_ref T_w (Section 4.1).
 // h_0 is returned as stored (shifted, see Inst).
-template <int SET>
-__device__ __forceinline__ void pull_set(const Lat& l, int x, int y, float abb, float v[9]) {
+template <int SET, typename ST = float, bool NC>
+__device__ __forceinline__ void pull_set(const LatT<NC>& l, int x, int y, float abb, float v[9],
+                                         const Ref& ref = Ref{0.f, 0.f}, float Cpref = 0.f,
+                                         float h0ref = 0.f, const float* pref = nullptr) {
+    constexpr bool kFref = sizeof(ST) != 4 && SET == 2;  // f: source-pressure reference
     const int own = y * l.pitch + x;
-    v[0] = ldA(l, 9 * SET, own);
+    v[0] = decode<ST, SET>(0, ldPop<ST>(l, 9 * SET, own), ref, Cpref, h0ref);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int xs = x - CX(i), ys = y - CY(i);
@@ -107,9 +174,11 @@ __device__ __forceinline__ void pull_set(const Lat& l, int x, int y, float abb, 
             else { wall = true; dir |= (l.flags & kDirYhi) != 0; }
         }
         if (!wall) {
-            v[i] = ldA(l, 9 * SET + i, ys * l.pitch + xs);
+            v[i] = decode<ST, SET>(i, ldPop<ST>(l, 9 * SET + i, ys * l.pitch + xs), ref, Cpref, h0ref);
+            if constexpr (kFref) v[i] += f_rest(i, pref[i]);
         } else {
-            float b = ldA(l, 9 * SET + OPP(i), own);
+            float b = decode<ST, SET>(OPP(i), ldPop<ST>(l, 9 * SET + OPP(i), own), ref, Cpref, h0ref);
+            if constexpr (kFref) b += f_rest(OPP(i), pref[0]);  // bounced: the site itself
             if (SET == 1 && dir) b = -b + 2.0f * WGT(i) * abb;
             v[i] = b;
         }
@@ -119,6 +188,8 @@ __device__ __forceinline__ void pull_set(const Lat& l, int x, int y, float abb, 
 struct Phys {
     float L, Hs, Tm, Cp, Cpref, Tw, omega_g, omega_h, kappa, beta, lam_coef;
     float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef, tan_w, inv_ramp, eps2;
+    float inv_L, inv_Cp;
+    float h0ref;   // Cp - (1 - w0) Cp_ref: T-coefficient of the rest h_0 (shifted)
 };
 
 __device__ __forceinline__ Phys load_phys(const Inst& I) {
@@ -128,6 +199,8 @@ __device__ __forceinline__ Phys load_phys(const Inst& I) {
     P.lam_coef = I.lam_coef; P.rho_s = I.rho_s; P.rho_l = I.rho_l; P.rho_g = I.rho_g;
     P.mu_s = I.mu_s; P.mu_l = I.mu_l; P.mu_g = I.mu_g; P.mdot_coef = I.mdot_coef;
     P.tan_w = I.tan_w; P.inv_ramp = I.inv_ramp; P.eps2 = I.normal_eps2;
+    P.inv_L = I.inv_L; P.inv_Cp = I.inv_Cp;
+    P.h0ref = I.Cp - (1.f - kW0) * I.Cpref;
     return P;
 }
 
@@ -136,7 +209,8 @@ __device__ __forceinline__ Phys load_phys(const Inst& I) {
 struct Macro {
     float Hp;    // shifted total enthalpy H'
     float fl, flp, fs, mdot, phi, rho;
-    bool mushy;  // H strictly between H_s and H_l: T = T_m exactly (Eq. 9b)
+    float T;     // Eq. 9b; inside the mushy range exactly T_m
+    bool mushy;  // H strictly between H_s and H_l
 };
 
 __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], const float h[9],
@@ -146,7 +220,7 @@ __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], co
 #pragma unroll
     for (int i = 0; i < 9; ++i) { phihat += g[i]; Hp += h[i]; }
     // Eq. 9a on the shifted enthalpy: (H - H_s)/L = (H' - H_s)/L + f_l^{n-1}
-    const float q = (Hp - P.Hs) / P.L + flp;
+    const float q = (Hp - P.Hs) * P.inv_L + flp;
     const float fl = clamp01(q);
     m.mushy = q > 0.0f && q < 1.0f;
     // solid only in the liquid content of the site
@@ -156,6 +230,10 @@ __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], co
     const float phi = phihat / (1.0f - 0.5f * mdot);    // Eq. 26
     m.Hp = Hp; m.fl = fl; m.flp = flp; m.fs = fs; m.mdot = mdot; m.phi = phi;
     m.rho = mix3(fs, phi, P.rho_s, P.rho_l, P.rho_g);   // Eq. 1
+    // Eq. 9b on the shifted enthalpy, H - H_s - L f_l = H' - H_s + L (f_l^{n-1}
+    // - f_l); inside the mushy range the exact value is T_m (evaluating the sum
+    // there would only add the rounding of f_l times L)
+    m.T = m.mushy ? P.Tm : P.Tm + (Hp - P.Hs + P.L * (flp - fl)) * P.inv_Cp;
     return m;
 }
 
@@ -193,31 +271,39 @@ __device__ void block_reduce_obs(double v[kObs], double* __restrict__ out) {
 // Per-site update shared by the tile and strip kernels
 // ---------------------------------------------------------------------------
 // Isotropic stencils of Eq. 38 at one site: gradients of phi, rho, p^{n-1},
-// S^{n-1} and the Laplacian of phi. Neighbours are accumulated in the order
-// i = 1..8 by every kernel (ghost values where a neighbour lies behind a
-// wall), then scaled by stencil_finish.
+// S^{n-1} and the Laplacian of phi.
 struct Stencil {
     float gphx, gphy, lph, grx, gry, gpx, gpy, gSx, gSy;
 };
 
-__device__ __forceinline__ void stencil_zero(Stencil& st) {
-    st.gphx = st.gphy = st.lph = st.grx = st.gry = st.gpx = st.gpy = st.gSx = st.gSy = 0.f;
+// Eq. 38 written with per-column combinations of rows y-1 (m), y (c) and
+// y+1 (p): with A = w1 c + w2 (p + m) and D = p - m of the columns x-1 (L),
+// x (C) and x+1 (R),
+//   grad_x = 3 (A_R - A_L),  grad_y = 3 (w1 D_C + w2 (D_R + D_L)),
+//   lap    = 6 (w1 ((c_R + c_L) + (p_C + m_C) - 4 c_C)
+//               + w2 ((p_R + m_R) + (p_L + m_L) - 4 c_C)).
+// Pairwise sums keep a uniform field exactly stencil-free in FP32. Both kernel
+// layouts evaluate exactly these expressions.
+struct ColSums {
+    float A, D;
+};
+__device__ __forceinline__ ColSums col_sums(float m, float c, float p) {
+    ColSums r;
+    r.A = kW1 * c + kW2 * (p + m);
+    r.D = p - m;
+    return r;
 }
-
-template <int I>
-__device__ __forceinline__ void stencil_acc(Stencil& st, float phi0, float zp, float zr,
-                                            float zq, float zs) {
-    constexpr float w = WGT(I);
-    st.gphx += w * CX(I) * zp; st.gphy += w * CY(I) * zp;
-    st.lph += w * (zp - phi0);
-    st.grx += w * CX(I) * zr; st.gry += w * CY(I) * zr;
-    st.gpx += w * CX(I) * zq; st.gpy += w * CY(I) * zq;
-    st.gSx += w * CX(I) * zs; st.gSy += w * CY(I) * zs;
+__device__ __forceinline__ void grad_cols(const ColSums& L, const ColSums& C, const ColSums& R,
+                                          float& gx, float& gy) {
+    gx = 3.f * (R.A - L.A);
+    gy = 3.f * (kW1 * C.D + kW2 * (R.D + L.D));
 }
-
-__device__ __forceinline__ void stencil_finish(Stencil& st) {
-    st.gphx *= 3.f; st.gphy *= 3.f; st.lph *= 6.f;
-    st.grx *= 3.f; st.gry *= 3.f; st.gpx *= 3.f; st.gpy *= 3.f; st.gSx *= 3.f; st.gSy *= 3.f;
+// cL, cR: row-y values of the side columns; sL, sC, sR: p + m of each column
+__device__ __forceinline__ float lap_cols(float cL, float cC, float cR, float sL, float sC,
+                                          float sR) {
+    const float t1 = (cR + cL) + sC - 4.f * cC;
+    const float t2 = (sR + sL) - 4.f * cC;
+    return 6.f * (kW1 * t1 + kW2 * t2);
 }
 
 // Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
@@ -225,13 +311,13 @@ __device__ __forceinline__ void stencil_finish(Stencil& st) {
 // post-collision populations and carried fields of one site. The order of
 // every floating-point operation is fixed here, so all kernels built on it
 // produce bit-identical results.
-template <bool OBS>
+template <bool OBS, typename ST = float>
 __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macro& m,
                                             const float g[9], const float h[9], const float f[9],
                                             float phiux_p, float phiuy_p, const Stencil& st,
-                                            float* __restrict__ B, float* __restrict__ Baux,
-                                            long long plane, int own, bool on_col, bool on_row,
-                                            double ob[kObs]) {
+                                            void* __restrict__ Bv, float* __restrict__ Baux,
+                                            int plane, int own, bool on_col, bool on_row,
+                                            double ob[kObs], const Ref* dref = nullptr) {
     const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
     const float gphx = st.gphx, gphy = st.gphy, lph = st.lph, grx = st.grx, gry = st.gry;
     const float gpx = st.gpx, gpy = st.gpy, gSx = st.gSx, gSy = st.gSy;
@@ -249,7 +335,8 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         my += CY(i) * f[i];
         if (i) fne0 += f[i];
     }
-    const float usx = (mx + 0.5f * Fx) / rho, usy = (my + 0.5f * Fy) / rho;
+    const float inv_rho = 1.f / rho;
+    const float usx = (mx + 0.5f * Fx) * inv_rho, usy = (my + 0.5f * Fy) * inv_rho;
     const float ffx = -fs * usx, ffy = -fs * usy;
     const float ux = usx + 0.5f * ffx, uy = usy + 0.5f * ffy;
     const float uu = ux * ux + uy * uy;
@@ -260,7 +347,7 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     const float Fty = Fy - gpy + (gry + gSy) * (1.f / 3.f);
     const float uFt = ux * Ftx + uy * Fty;
     const float mu = mix3(fs, phi, P.mu_s, P.mu_l, P.mu_g);
-    const float tau_f = mu / (rho * (1.f / 3.f)) + 0.5f;
+    const float tau_f = 3.f * mu * inv_rho + 0.5f;
     const float omega_f = 1.f / tau_f;
     const float Fpx = Fx + rho * ffx, Fpy = Fy + rho * ffy;  // F + rho f
     const float F0 = kW0 * (S - 3.f * uFt);
@@ -281,18 +368,20 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     const float gsrc = 1.f - 0.5f * P.omega_g;
     const float pmd = phi * mdot;
 
-    // Enthalpy: T from Eq. 9b on the shifted enthalpy,
-    // H - H_s - L f_l = H' - H_s + L (f_l^{n-1} - f_l); inside the mushy
-    // range the exact value is T_m (evaluating the sum there would only
-    // add the rounding of f_l times L)
+    // Enthalpy (T from the local macroscopic step)
     const float dL = P.L * (m.flp - m.fl);
-    const float T = m.mushy ? P.Tm : P.Tm + (m.Hp - P.Hs + dL) / P.Cp;
+    const float T = m.T;
 
     const float fsrc = 1.f - 0.5f * omega_f;
+    const float TCp = T * P.Cp, TCpref = T * P.Cpref;
+    const float uu15 = 1.5f * uu;
+    float g0n = 0.f, h0n = 0.f, f0n = 0.f, eg = 0.f, eh = 0.f, ef = 0.f;  // FP16 storage
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float w = WGT(i);
         const float cu = CX(i) * ux + CY(i) * uy;
+        // s_i(u) of Eq. 32, shared by the flow and enthalpy equilibria
+        const float si = w * (3.f * cu + 4.5f * cu * cu - uu15);
         // g (Eqs. 21, 24, 25)
         const float geq = w * phi * (1.f + 3.f * cu);
         const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
@@ -300,27 +389,58 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         // h (Eqs. 27-28); h_0 carried shifted by -L f_l
         float hn;
         if (i == 0) {
-            const float heq0 = m.Hp + dL - P.Cpref * T + kW0 * T * (P.Cpref - P.Cp * 1.5f * uu);
+            const float heq0 = m.Hp + dL - TCpref + kW0 * (TCpref - TCp * uu15);
             hn = (1.f - P.omega_h) * (h[0] + dL) + P.omega_h * heq0;
         } else {
-            const float heq = w * T * (P.Cpref + P.Cp * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const float heq = w * TCpref + TCp * si;
             hn = h[i] - P.omega_h * (h[i] - heq);
         }
         // f (Eqs. 30-33)
-        const float si = w * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
         const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
         const float cF = CX(i) * Ftx + CY(i) * Fty;
         const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
         const float fn = f[i] - omega_f * (f[i] - feq) + fsrc * Fi;
-        B[(long long)(i) * plane + own] = gn;
-        B[(long long)(9 + i) * plane + own] = hn;
-        B[(long long)(18 + i) * plane + own] = fn;
+        if constexpr (sizeof(ST) == 4) {
+            float* B = static_cast<float*>(Bv);
+            B[i * plane + own] = gn;
+            B[(9 + i) * plane + own] = hn;
+            B[(18 + i) * plane + own] = fn;
+        } else {
+            if (i == 0) {
+                g0n = gn; h0n = hn; f0n = fn;
+            } else {
+                // deviations from the rest equilibria (g, h: destination's
+                // references dref[i]; f: this site's pressure), and the error
+                // the destination will see after decoding
+                __half* B = static_cast<__half*>(Bv);
+                const Ref& d = dref[i];
+                const float rg = w * d.phi, rh = w * P.Cpref * d.T, rf = f_rest(i, pn);
+                const __half qg = __float2half_rn(gn - rg);
+                const __half qh = __float2half_rn(hn - rh);
+                const __half qf = __float2half_rn((fn - rf) * kFScale);
+                B[i * plane + own] = qg;
+                B[(9 + i) * plane + own] = qh;
+                B[(18 + i) * plane + own] = qf;
+                eg += (__half2float(qg) + rg) - gn;
+                eh += (__half2float(qh) + rh) - hn;
+                ef += (__half2float(qf) * kInvFScale + rf) - fn;
+            }
+        }
+    }
+    if constexpr (sizeof(ST) != 4) {
+        Baux[7 * plane + own] = g0n - eg;
+        Baux[8 * plane + own] = h0n - eh;
+        Baux[9 * plane + own] = f0n - ef;
     }
     Baux[own] = m.fl;
     Baux[plane + own] = phiux;
     Baux[2 * plane + own] = phiuy;
     Baux[3 * plane + own] = pn;
     Baux[4 * plane + own] = S;
+    if constexpr (sizeof(ST) != 4) {
+        Baux[5 * plane + own] = phi;  // references of this site for the next step
+        Baux[6 * plane + own] = T;
+    }
 
     if (OBS) {
         const double dphi = phi, dfs = fs;
@@ -356,7 +476,7 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
     Lat l;
     l.A = static_cast<const float*>(I.pop[parity]);
     l.Aaux = I.aux[parity];
-    l.plane = I.plane; l.nx = I.nx; l.ny = I.ny; l.pitch = I.pitch; l.flags = I.flags;
+    l.plane = (int)I.plane; l.nx = I.nx; l.ny = I.ny; l.pitch = I.pitch; l.flags = I.flags;
     float* __restrict__ B = static_cast<float*>(I.pop[parity ^ 1]);
     float* __restrict__ Baux = I.aux[parity ^ 1];
     const float abb = P.Cpref * P.Tw;
@@ -512,16 +632,29 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
     }
     if (active) {
         Stencil st;
-        stencil_zero(st);
-#define LBM_TILE_ACC(I)                                                                  \
-    {                                                                                    \
-        const int sidx = SI(tx + CX(I), ty + CY(I));                                     \
-        stencil_acc<I>(st, m.phi, s_phi[sidx], s_rho[sidx], s_p[sidx], s_S[sidx]);       \
-    }
-        LBM_TILE_ACC(1) LBM_TILE_ACC(2) LBM_TILE_ACC(3) LBM_TILE_ACC(4)
-        LBM_TILE_ACC(5) LBM_TILE_ACC(6) LBM_TILE_ACC(7) LBM_TILE_ACC(8)
-#undef LBM_TILE_ACC
-        stencil_finish(st);
+        {
+            // column sums of x-1, x, x+1 from shared memory (same expressions as
+            // the strip kernel's shuffled column sums)
+            auto col = [&](const float* a, int dx, float& m_, float& c_, float& p_) {
+                m_ = a[SI(tx + dx, ty - 1)];
+                c_ = a[SI(tx + dx, ty)];
+                p_ = a[SI(tx + dx, ty + 1)];
+            };
+            float mL, cL, pL, mC, cC, pC, mR, cR, pR;
+            col(s_phi, -1, mL, cL, pL); col(s_phi, 0, mC, cC, pC); col(s_phi, 1, mR, cR, pR);
+            grad_cols(col_sums(mL, cL, pL), col_sums(mC, cC, pC), col_sums(mR, cR, pR),
+                      st.gphx, st.gphy);
+            st.lph = lap_cols(cL, cC, cR, pL + mL, pC + mC, pR + mR);
+            col(s_rho, -1, mL, cL, pL); col(s_rho, 0, mC, cC, pC); col(s_rho, 1, mR, cR, pR);
+            grad_cols(col_sums(mL, cL, pL), col_sums(mC, cC, pC), col_sums(mR, cR, pR),
+                      st.grx, st.gry);
+            col(s_p, -1, mL, cL, pL); col(s_p, 0, mC, cC, pC); col(s_p, 1, mR, cR, pR);
+            grad_cols(col_sums(mL, cL, pL), col_sums(mC, cC, pC), col_sums(mR, cR, pR),
+                      st.gpx, st.gpy);
+            col(s_S, -1, mL, cL, pL); col(s_S, 0, mC, cC, pC); col(s_S, 1, mR, cR, pR);
+            grad_cols(col_sums(mL, cL, pL), col_sums(mC, cC, pC), col_sums(mR, cR, pR),
+                      st.gSx, st.gSy);
+        }
         site_update<OBS>(P, l.flags, m, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
                          y * l.pitch + x, x == l.nx / 2, y == l.ny / 2, ob);
     }
@@ -566,15 +699,18 @@ step_tile_noalloc(const Inst I, int tiles_x, double* __restrict__ partials) {
 
 // Pull of set SET at (x, y) for a row whose sources do not cross a wall; the
 // column offsets xm/xp and row offsets rm/rp are already wrapped.
-template <int SET>
-__device__ __forceinline__ void pull_rows(const Lat& l, int xc, int xm, int xp, int r0,
-                                          int rm, int rp, float v[9]) {
-    const float* __restrict__ A = l.A + (long long)(9 * SET) * l.plane;
+template <int SET, typename ST, bool NC>
+__device__ __forceinline__ void pull_rows(const LatT<NC>& l, int xc, int xm, int xp, int r0,
+                                          int rm, int rp, float v[9], const Ref& ref,
+                                          float Cpref, float h0ref, const float* pref) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int r = CY(i) > 0 ? rm : (CY(i) < 0 ? rp : r0);   // source row y - cy
         const int c = CX(i) > 0 ? xm : (CX(i) < 0 ? xp : xc);   // source column x - cx
-        v[i] = __ldg(A + (long long)i * l.plane + r + c);
+        v[i] = decode<ST, SET>(i, ldPop<ST>(l, 9 * SET + i, r + c), ref, Cpref, h0ref);
+        if constexpr (sizeof(ST) != 4 && SET == 2) {
+            if (i) v[i] += f_rest(i, pref[i]);
+        }
     }
 }
 
@@ -584,15 +720,18 @@ struct RowCtx {
 };
 
 // Pulls and local macroscopic fields of lattice row y at this lane's column.
-template <int SET>
-__device__ __forceinline__ void pull_row(const Lat& l, const RowCtx& c, int y, float abb,
-                                         float v[9]) {
+template <int SET, typename ST = float, bool NC>
+__device__ __forceinline__ void pull_row(const LatT<NC>& l, const RowCtx& c, int y, float abb,
+                                         float v[9], const Ref& ref = Ref{0.f, 0.f},
+                                         float Cpref = 0.f, float h0ref = 0.f,
+                                         const float* pref = nullptr) {
     if (c.py || (y >= 1 && y <= l.ny - 2)) {
         const int ym = y == 0 ? l.ny - 1 : y - 1;
         const int yp = y == l.ny - 1 ? 0 : y + 1;
-        pull_rows<SET>(l, c.xc, c.xm, c.xp, y * l.pitch, ym * l.pitch, yp * l.pitch, v);
+        pull_rows<SET, ST>(l, c.xc, c.xm, c.xp, y * l.pitch, ym * l.pitch, yp * l.pitch, v, ref,
+                           Cpref, h0ref, pref);
     } else {
-        pull_set<SET>(l, c.xc, y, abb, v);
+        pull_set<SET, ST>(l, c.xc, y, abb, v, ref, Cpref, h0ref, pref);
     }
 }
 
@@ -617,21 +756,19 @@ __device__ __forceinline__ float strip_wet_ghost(float a, float b, float outer_a
     return a + tan_w * fabsf(1.5f * d0 - 0.5f * d1);
 }
 
-template <int WARPS, int MINB, bool OBS>
-__global__ void __launch_bounds__(WARPS * 32, MINB)
-step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
-           int parity, double* __restrict__ partials) {
+// One warp advances strip item W by one step (the body of every strip kernel).
+template <bool OBS, typename ST, bool NC>
+__device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const Item& W,
+                                           int parity, double* __restrict__ partials) {
+    constexpr bool kHalf = sizeof(ST) != 4;
     const int lane = threadIdx.x & 31;
-    const int it = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (it >= n_items) return;  // whole warp leaves together; no block barrier below
-    const Item W = items[it];
     const Inst& I = insts[W.inst];
     const Phys P = load_phys(I);
-    Lat l;
+    LatT<NC> l;
     l.A = static_cast<const float*>(I.pop[parity]);
     l.Aaux = I.aux[parity];
-    l.plane = I.plane; l.nx = I.nx; l.ny = I.ny; l.pitch = I.pitch; l.flags = I.flags;
-    float* __restrict__ B = static_cast<float*>(I.pop[parity ^ 1]);
+    l.plane = (int)I.plane; l.nx = I.nx; l.ny = I.ny; l.pitch = I.pitch; l.flags = I.flags;
+    void* __restrict__ B = I.pop[parity ^ 1];
     float* __restrict__ Baux = I.aux[parity ^ 1];
     const float abb = P.Cpref * P.Tw;
     const int nx = l.nx, ny = l.ny;
@@ -646,13 +783,22 @@ step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n
     const bool halo_lane = lane == 0 || lane == 31;
     const int x_outer = lane == 0 ? c.xm : c.xp;   // one column beyond the strip
 
+    // decoding references of a site (FP16 storage)
+    auto site_ref = [&](int idx) {
+        Ref r{0.f, 0.f};
+        if constexpr (kHalf) { r.phi = ldAux(l, 5, idx); r.T = ldAux(l, 6, idx); }
+        return r;
+    };
+
     // phi one column beyond the strip at the wall-adjacent rows (halo lanes)
     float oB0 = 0.f, oB1 = 0.f, oT0 = 0.f, oT1 = 0.f;
     auto outer_phi = [&](int y) {
         float gg[9], hh[9];
-        pull_set<0>(l, x_outer, y, abb, gg);
-        pull_set<1>(l, x_outer, y, abb, hh);
-        return local_macro(P, gg, hh, ldAux(l, 0, y * l.pitch + x_outer)).phi;
+        const int idx = y * l.pitch + x_outer;
+        const Ref r = site_ref(idx);
+        pull_set<0, ST>(l, x_outer, y, abb, gg, r, P.Cpref, P.h0ref);
+        pull_set<1, ST>(l, x_outer, y, abb, hh, r, P.Cpref, P.h0ref);
+        return local_macro(P, gg, hh, ldAux(l, 0, idx)).phi;
     };
     auto note_outer = [&](int y) {
         if (c.py || !halo_lane) return;
@@ -663,11 +809,12 @@ step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n
     };
     // local macroscopic fields of row y at this lane's column (the pulled g
     // and h are dropped; the collision of the row pulls them again, from L1)
-    auto row_macro = [&](int y, Macro& m, float& p, float& S) {
+    auto row_macro = [&](int y, Macro& m, float& p, float& S, Ref& r) {
         float gg[9], hh[9];
-        pull_row<0>(l, c, y, abb, gg);
-        pull_row<1>(l, c, y, abb, hh);
         const int idx = y * l.pitch + c.xc;
+        r = site_ref(idx);
+        pull_row<0, ST>(l, c, y, abb, gg, r, P.Cpref, P.h0ref);
+        pull_row<1, ST>(l, c, y, abb, hh, r, P.Cpref, P.h0ref);
         m = local_macro(P, gg, hh, ldAux(l, 0, idx));
         p = ldAux(l, 3, idx);
         S = ldAux(l, 4, idx);
@@ -680,67 +827,117 @@ step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n
         for (int j = 0; j < kObs; ++j) ob[j] = 0.0;
     }
 
-    // rows y-1 (m), y (0) and y+1 (p) of phi, rho, p^{n-1}, S^{n-1}
+    // rows y-1 (m), y (0) and y+1 (p) of phi, rho, p^{n-1}, S^{n-1} (and T)
     float phm = 0.f, ph0, php = 0.f, rhm = 0.f, rh0, rhp = 0.f;
     float pm = 0.f, p0, pp = 0.f, Sm = 0.f, S0, Sp = 0.f;
+    float tm = 0.f, t0, tp = 0.f;
     Macro mO;
+    Ref rO;
     const int y0 = W.y0;
-    row_macro(y0, mO, p0, S0);
-    ph0 = mO.phi; rh0 = mO.rho;
+    row_macro(y0, mO, p0, S0, rO);
+    ph0 = mO.phi; rh0 = mO.rho; t0 = mO.T;
     if (y0 >= 1 || c.py) {
         Macro mm;
-        row_macro(y0 == 0 ? ny - 1 : y0 - 1, mm, pm, Sm);
-        phm = mm.phi; rhm = mm.rho;
+        Ref rr;
+        row_macro(y0 == 0 ? ny - 1 : y0 - 1, mm, pm, Sm, rr);
+        phm = mm.phi; rhm = mm.rho; tm = mm.T;
     }
 
     for (int y = y0; y < W.y1; ++y) {
+        const int own = y * l.pitch + c.xc;
+        // Every load that goes to DRAM for this row is issued here, before any
+        // of it is consumed: f and (phi u)^{n-1} of row y, then g, h and the
+        // carried scalars of row y+1 (inside row_macro).
+        float f[9];
+        float pref[9];
+        // FP16 storage: pressures of the sites the pulled f come from (rows
+        // y-1..y+1 of the carried p, neighbouring lanes); links that bounce
+        // at a wall use the site's own pressure (pref[0]). Valid once the
+        // window holds row y+1, i.e. after the look-ahead below.
+        auto pull_f = [&]() {
+            if constexpr (kHalf) {
+                pref[0] = p0;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const int cy = CY(i);
+                    const float v = cy > 0 ? pm : (cy < 0 ? pp : p0);  // source row y - cy
+                    pref[i] = lane_shift(v, -CX(i));                     // source column x - cx
+                }
+            }
+            pull_row<2, ST>(l, c, y, abb, f, rO, P.Cpref, P.h0ref, pref);
+        };
+        if constexpr (!kHalf) pull_f();
+        const float phiux_p = ldAux(l, 1, own), phiuy_p = ldAux(l, 2, own);
         Macro mN;
-        if (y + 1 < ny || c.py) {
-            row_macro(y + 1 == ny ? 0 : y + 1, mN, pp, Sp);
-            php = mN.phi; rhp = mN.rho;
+        Ref rN{0.f, 0.f};
+        const bool top_wall = !(y + 1 < ny || c.py);
+        if (!top_wall) {
+            row_macro(y + 1 == ny ? 0 : y + 1, mN, pp, Sp, rN);
+            php = mN.phi; rhp = mN.rho; tp = mN.T;
         } else {
             // row ny lies behind the top wall: ghost from rows ny-1 and ny-2
             php = strip_wet_ghost(ph0, phm, oT0, oT1, lane, P.tan_w);
-            rhp = rh0; pp = p0; Sp = S0;
+            rhp = rh0; pp = p0; Sp = S0; tp = t0;
         }
-        if (y == 0 && !c.py) {
+        const bool bottom_wall = y == 0 && !c.py;
+        if (bottom_wall) {
             // row -1 lies behind the bottom wall: ghost from rows 0 and 1
             phm = strip_wet_ghost(ph0, php, oB0, oB1, lane, P.tan_w);
-            rhm = rh0; pm = p0; Sm = S0;
+            rhm = rh0; pm = p0; Sm = S0; tm = t0;
+        }
+        if constexpr (kHalf) pull_f();
+
+        // Eq. 38 from column sums exchanged with the neighbouring lanes
+        Stencil st;
+        {
+            const float sph = php + phm;
+            const ColSums cph = col_sums(phm, ph0, php), crh = col_sums(rhm, rh0, rhp);
+            const ColSums cpp = col_sums(pm, p0, pp), cSS = col_sums(Sm, S0, Sp);
+            auto side = [](const ColSums& v, int dx) {
+                ColSums r;
+                r.A = lane_shift(v.A, dx);
+                r.D = lane_shift(v.D, dx);
+                return r;
+            };
+            grad_cols(side(cph, -1), cph, side(cph, 1), st.gphx, st.gphy);
+            st.lph = lap_cols(lane_shift(ph0, -1), ph0, lane_shift(ph0, 1), lane_shift(sph, -1),
+                              sph, lane_shift(sph, 1));
+            grad_cols(side(crh, -1), crh, side(crh, 1), st.grx, st.gry);
+            grad_cols(side(cpp, -1), cpp, side(cpp, 1), st.gpx, st.gpy);
+            grad_cols(side(cSS, -1), cSS, side(cSS, 1), st.gSx, st.gSy);
         }
 
-        Stencil st;
-        stencil_zero(st);
-#define LBM_STRIP_ACC(I)                                                                 \
-    {                                                                                    \
-        constexpr int cy = CY(I);                                                        \
-        const float vphi = cy > 0 ? php : (cy < 0 ? phm : ph0);                          \
-        const float vrho = cy > 0 ? rhp : (cy < 0 ? rhm : rh0);                          \
-        const float vp = cy > 0 ? pp : (cy < 0 ? pm : p0);                               \
-        const float vS = cy > 0 ? Sp : (cy < 0 ? Sm : S0);                               \
-        stencil_acc<I>(st, ph0, lane_shift(vphi, CX(I)), lane_shift(vrho, CX(I)),        \
-                       lane_shift(vp, CX(I)), lane_shift(vS, CX(I)));                    \
-    }
-        LBM_STRIP_ACC(1) LBM_STRIP_ACC(2) LBM_STRIP_ACC(3) LBM_STRIP_ACC(4)
-        LBM_STRIP_ACC(5) LBM_STRIP_ACC(6) LBM_STRIP_ACC(7) LBM_STRIP_ACC(8)
-#undef LBM_STRIP_ACC
-        stencil_finish(st);
+        // FP16 storage: references of the sites each outgoing population
+        // streams into (the site itself where the link bounces at a wall)
+        Ref dref[9];
+        if constexpr (kHalf) {
+            dref[0] = Ref{ph0, t0};
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int cy = CY(i);
+                const float vp = cy > 0 ? php : (cy < 0 ? phm : ph0);
+                const float vt = cy > 0 ? tp : (cy < 0 ? tm : t0);
+                const float sp = lane_shift(vp, CX(i)), stt = lane_shift(vt, CX(i));
+                const bool wall = (cy > 0 && top_wall) || (cy < 0 && bottom_wall);
+                dref[i] = wall ? Ref{ph0, t0} : Ref{sp, stt};
+            }
+        }
 
         if (out_lane) {
-            float g[9], h[9], f[9];
-            pull_row<0>(l, c, y, abb, g);
-            pull_row<1>(l, c, y, abb, h);
-            pull_row<2>(l, c, y, abb, f);
-            const int own = y * l.pitch + c.xc;
-            const float phiux_p = ldAux(l, 1, own), phiuy_p = ldAux(l, 2, own);
-            site_update<OBS>(P, l.flags, mO, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
-                             own, c.xc == nx / 2, y == ny / 2, ob);
+            // g and h of row y were pulled one row earlier: these loads hit L1
+            float g[9], h[9];
+            pull_row<0, ST>(l, c, y, abb, g, rO, P.Cpref, P.h0ref);
+            pull_row<1, ST>(l, c, y, abb, h, rO, P.Cpref, P.h0ref);
+            site_update<OBS, ST>(P, l.flags, mO, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
+                                 own, c.xc == nx / 2, y == ny / 2, ob, dref);
         }
 
         // advance the window
         phm = ph0; ph0 = php; rhm = rh0; rh0 = rhp;
         pm = p0; p0 = pp; Sm = S0; S0 = Sp;
+        tm = t0; t0 = tp;
         mO = mN;
+        rO = rN;
     }
 
     if (OBS) {
@@ -755,6 +952,84 @@ step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n
             if (lane == 0) partials[(long long)W.part * kObs + j] = v;
         }
     }
+}
+
+template <int WARPS, int MINB, bool OBS, typename ST>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
+           int parity, double* __restrict__ partials) {
+    const int it = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (it >= n_items) return;  // whole warp leaves together; no block barrier in the body
+    strip_item<OBS, ST, true>(insts, items[it], parity, partials);
+}
+
+// Device-wide barrier between the steps of the persistent kernel. Every CTA
+// of the (cooperatively launched, hence co-resident) grid adds one to *bar
+// and waits until it reaches `target`. The wait is bounded in time and in
+// iterations: past either bound the CTA raises *err and returns false, as
+// does every CTA that finds *err raised, so no CTA waits for a step that
+// will not come.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* err,
+                                             unsigned long long limit_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        unsigned long long t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (unsigned spin = 0;; ++spin) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if ((spin & 31u) == 31u) {
+                int e;
+                asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (e != 0) { ok = 0; break; }
+                if (t - t0 > limit_ns || spin > (1u << 26)) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Persistent form: one cooperative launch advances every item of every
+// lattice by `nsteps` steps (parity alternating from parity0), each warp
+// taking items in grid-stride order, with a device-wide barrier between
+// steps. *bar must be zero at launch.
+template <int WARPS, int MINB, typename ST>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+step_strip_persistent(const Inst* __restrict__ insts, const Item* __restrict__ items,
+                      int n_items, int parity0, int nsteps, unsigned* bar, int* err,
+                      unsigned long long limit_ns) {
+    const int warp = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const int stride = gridDim.x * WARPS;
+    for (int s = 0; s < nsteps; ++s) {
+        const int parity = parity0 ^ (s & 1);
+        for (int it = warp; it < n_items; it += stride)
+            strip_item<false, ST, false>(insts, items[it], parity, nullptr);
+        if (s + 1 < nsteps &&
+            !grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, err, limit_ns))
+            return;
+    }
+}
+
+// A barrier that no other CTA joins: the single CTA of this kernel waits for
+// a count of two until the time limit, raises *err and returns. Used to check
+// that an expired wait is reported to the host rather than hanging.
+__global__ void barrier_timeout_probe(unsigned* bar, int* err, unsigned long long limit_ns) {
+    grid_barrier(bar, 2u, err, limit_ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -789,6 +1064,69 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
         A[2 * I.plane + idx] = 0.f;
         A[3 * I.plane + idx] = 0.f;
         A[4 * I.plane + idx] = 0.f;
+    }
+}
+
+// FP16 storage: the same equilibrium start, each population stored as its
+// deviation from the rest-equilibrium reference of the site it streams into.
+__device__ __forceinline__ double init_T(const InitConst& c, double T0) {
+    const double H = c.Cp * T0 + c.L;
+    double fl = (H - c.Hs) / c.L;
+    fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
+    return c.Tm + (H - c.Hs - c.L * fl) / c.Cp;
+}
+
+__global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
+                          const double* __restrict__ phi0, const double* __restrict__ T0,
+                          int parity) {
+    const Inst& I = insts[inst];
+    const int n = I.nx * I.ny;
+    const int plane = (int)I.plane;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int x = k % I.nx, y = k / I.nx;
+        const int idx = y * I.pitch + x;
+        const double ph = phi0[k];
+        const double H = c.Cp * T0[k] + c.L;
+        double fl = (H - c.Hs) / c.L;
+        fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
+        const double T = c.Tm + (H - c.Hs - c.L * fl) / c.Cp;
+        __half* P = static_cast<__half*>(I.pop[parity]);
+        float* A = I.aux[parity];
+        const float phr = (float)ph, Tr = (float)T;
+        for (int i = 0; i < 9; ++i) {
+            const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+            const float wf = WGT(i);
+            // destination of the link (the site itself behind a wall)
+            int xd = x + CX(i), yd = y + CY(i);
+            bool wall = false;
+            if (xd < 0 || xd >= I.nx) {
+                if (I.flags & kPeriodicX) xd = (xd + I.nx) % I.nx; else wall = true;
+            }
+            if (yd < 0 || yd >= I.ny) {
+                if (I.flags & kPeriodicY) yd = (yd + I.ny) % I.ny; else wall = true;
+            }
+            const int kd = wall ? k : yd * I.nx + xd;
+            const float phd = (float)phi0[kd];
+            const float Td = (float)init_T(c, T0[kd]);
+            if (i == 0) {  // rest populations in FP32
+                A[7 * plane + idx] = (float)(w * ph);                                 // Eq. 24
+                A[8 * plane + idx] =
+                    (float)(H - c.Cpref * T + w * c.Cp * T * (c.Cpref / c.Cp) - c.L * fl);  // shifted h_0
+                A[9 * plane + idx] = 0.f;
+                continue;
+            }
+            P[i * plane + idx] = __double2half(w * ph - (double)(wf * phd));      // Eq. 24, u = 0
+            P[(9 + i) * plane + idx] =
+                __double2half(w * c.Cp * T * (c.Cpref / c.Cp) - (double)(wf * I.Cpref * Td));  // Eq. 28
+            P[(18 + i) * plane + idx] = __float2half_rn(0.f);  // Eq. 31 vanishes at p = 0, u = 0
+        }
+        A[idx] = (float)fl;
+        A[plane + idx] = 0.f;
+        A[2 * plane + idx] = 0.f;
+        A[3 * plane + idx] = 0.f;
+        A[4 * plane + idx] = 0.f;
+        A[5 * plane + idx] = phr;
+        A[6 * plane + idx] = Tr;
     }
 }
 
@@ -847,32 +1185,113 @@ cudaError_t launch_tile(const Inst* d_inst, const Tile* d_tiles, int n_tiles, in
     return cudaGetLastError();
 }
 
-template <int WARPS, int MINB>
+template <int WARPS, int MINB, typename ST>
 cudaError_t launch_strip_w(const Inst* d_inst, const Item* d_items, int n_items, int parity,
                            int obs, double* d_partials, cudaStream_t s) {
     const int blocks = (n_items + WARPS - 1) / WARPS;
     if (obs)
-        step_strip<WARPS, MINB, true><<<blocks, WARPS * 32, 0, s>>>(d_inst, d_items, n_items, parity,
-                                                                   d_partials);
+        step_strip<WARPS, MINB, true, ST><<<blocks, WARPS * 32, 0, s>>>(d_inst, d_items, n_items,
+                                                                       parity, d_partials);
     else
-        step_strip<WARPS, MINB, false><<<blocks, WARPS * 32, 0, s>>>(d_inst, d_items, n_items, parity,
-                                                                    d_partials);
+        step_strip<WARPS, MINB, false, ST><<<blocks, WARPS * 32, 0, s>>>(d_inst, d_items, n_items,
+                                                                        parity, d_partials);
     return cudaGetLastError();
+}
+
+// Persistent launches: the kernel of a (warps, regs, storage) variant, and
+// the co-resident grid for it.
+template <int WARPS, int MINB, typename ST>
+struct Persist {
+    static void* fn() { return reinterpret_cast<void*>(&step_strip_persistent<WARPS, MINB, ST>); }
+    static int grid(int n_items) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_strip_persistent<WARPS, MINB, ST>,
+                                                          WARPS * 32, 0) != cudaSuccess)
+            return 0;
+        const int want = (n_items + WARPS - 1) / WARPS;
+        return std::max(1, std::min(want, per_sm * sms));
+    }
+    static cudaError_t launch(int grid, const Inst* d_inst, const Item* d_items, int n_items,
+                              int parity0, int nsteps, unsigned* bar, int* err,
+                              unsigned long long limit_ns, cudaStream_t s) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(WARPS * 32);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, step_strip_persistent<WARPS, MINB, ST>, d_inst, d_items,
+                                  n_items, parity0, nsteps, bar, err, limit_ns);
+    }
+};
+
+// Dispatch of a persistent call F over the supported strip variants.
+template <typename ST, typename F>
+auto persist_dispatch(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, ST>())) {
+    if (warps == 4 && regs == 128) return f(Persist<4, 4, ST>());
+    if (warps == 4 && regs == 168) return f(Persist<4, 3, ST>());
+    if (warps == 4 && regs == 255) return f(Persist<4, 1, ST>());
+    if (warps == 8 && regs == 128) return f(Persist<8, 2, ST>());
+    return f(Persist<2, 8, ST>());
+}
+
+template <typename ST>
+cudaError_t launch_strip_st(int warps, int regs, const Inst* d_inst, const Item* d_items,
+                            int n_items, int parity, int obs, double* d_partials, cudaStream_t s) {
+    // regs: register budget per thread (128, 168 or 255) via the minimum
+    // number of resident CTAs requested from the compiler
+    if (warps == 4 && regs == 128) return launch_strip_w<4, 4, ST>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 4 && regs == 168) return launch_strip_w<4, 3, ST>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 4 && regs == 255) return launch_strip_w<4, 1, ST>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 8 && regs == 128) return launch_strip_w<8, 2, ST>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (warps == 2 && regs == 128) return launch_strip_w<2, 8, ST>(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_step_strip(int warps, int regs, const Inst* d_inst, const Item* d_items,
-                              int n_items, int parity, int obs, double* d_partials, cudaStream_t s) {
+cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_inst,
+                              const Item* d_items, int n_items, int parity, int obs,
+                              double* d_partials, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
-    // regs: register budget per thread (128, 168 or 255) via the minimum
-    // number of resident CTAs requested from the compiler
-    if (warps == 4 && regs == 128) return launch_strip_w<4, 4>(d_inst, d_items, n_items, parity, obs, d_partials, s);
-    if (warps == 4 && regs == 168) return launch_strip_w<4, 3>(d_inst, d_items, n_items, parity, obs, d_partials, s);
-    if (warps == 4 && regs == 255) return launch_strip_w<4, 1>(d_inst, d_items, n_items, parity, obs, d_partials, s);
-    if (warps == 8 && regs == 128) return launch_strip_w<8, 2>(d_inst, d_items, n_items, parity, obs, d_partials, s);
-    if (warps == 2 && regs == 128) return launch_strip_w<2, 8>(d_inst, d_items, n_items, parity, obs, d_partials, s);
-    return cudaErrorInvalidValue;
+    if (storage == LBM_STORE_FP16)
+        return launch_strip_st<__half>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials, s);
+    if (storage != LBM_STORE_FP32) return cudaErrorNotSupported;
+    return launch_strip_st<float>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials, s);
+}
+
+int persistent_grid(int warps, int regs, int storage, int n_items) {
+    if (!strip_supported(warps, regs) || n_items <= 0) return 0;
+    auto g = [&](auto v) { return decltype(v)::grid(n_items); };
+    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(warps, regs, g);
+    return persist_dispatch<float>(warps, regs, g);
+}
+
+cudaError_t launch_step_strip_persistent(int warps, int regs, int storage, int grid,
+                                         const Inst* d_inst, const Item* d_items, int n_items,
+                                         int parity0, int nsteps, unsigned* d_bar, int* d_err,
+                                         unsigned long long limit_ns, cudaStream_t s) {
+    if (!strip_supported(warps, regs) || grid <= 0) return cudaErrorInvalidValue;
+    if (n_items <= 0 || nsteps <= 0) return cudaSuccess;
+    auto go = [&](auto v) {
+        return decltype(v)::launch(grid, d_inst, d_items, n_items, parity0, nsteps, d_bar, d_err,
+                                   limit_ns, s);
+    };
+    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(warps, regs, go);
+    if (storage != LBM_STORE_FP32) return cudaErrorNotSupported;
+    return persist_dispatch<float>(warps, regs, go);
+}
+
+cudaError_t launch_barrier_timeout_probe(unsigned* d_bar, int* d_err, unsigned long long limit_ns,
+                                         cudaStream_t s) {
+    barrier_timeout_probe<<<1, 32, 0, s>>>(d_bar, d_err, limit_ns);
+    return cudaGetLastError();
 }
 
 bool strip_supported(int warps, int regs) {
@@ -912,12 +1331,16 @@ cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partia
 
 cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage, InitConst c,
                         const double* d_phi0, const double* d_T0, int parity, cudaStream_t s) {
-    if (storage != 0) return cudaErrorNotSupported;
     const int threads = 256;
     int blocks = (n_sites + threads - 1) / threads;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    init_fp32<<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
+    if (storage == LBM_STORE_FP32)
+        init_fp32<<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
+    else if (storage == LBM_STORE_FP16)
+        init_fp16<<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
+    else
+        return cudaErrorNotSupported;
     return cudaGetLastError();
 }
 

@@ -63,8 +63,10 @@ SYMBOLS = (
     "lbm_observables", "lbm_observables_all", "lbm_get_state", "lbm_set_state",
     "lbm_step_count", "lbm_launch_count", "lbm_destroy", "lbm_error_string",
     "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune", "lbm_step_noalloc",
+    "lbm_set_exec", "lbm_get_exec", "lbm_barrier_selftest",
 )
 LBM_KERNEL_TILE, LBM_KERNEL_STRIP = 0, 1
+LBM_EXEC_LAUNCH, LBM_EXEC_GRAPH, LBM_EXEC_PERSISTENT = 0, 1, 2
 
 
 def load(path: str | None = None):
@@ -103,6 +105,9 @@ def load(path: str | None = None):
         lib.lbm_autotune.restype = ctypes.c_int
         lib.lbm_step_noalloc.argtypes = [P(lbm_params), vp, vp, vp, vp, i32, vp, vp]
         lib.lbm_step_noalloc.restype = ctypes.c_int
+        lib.lbm_set_exec.argtypes = [vp, i32, i32]
+        lib.lbm_get_exec.argtypes = [vp, P(i32)]
+        lib.lbm_barrier_selftest.argtypes = [vp, u64, P(i32)]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in ("lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
@@ -244,6 +249,29 @@ def lbm_get_kernel(h):
     return tuple(out[:])
 
 
+def lbm_set_exec(h, mode: int, chunk: int = 64):
+    rc = load().lbm_set_exec(h, int(mode), int(chunk))
+    if rc:
+        raise LbmError(rc, "lbm_set_exec")
+
+
+def lbm_get_exec(h):
+    """(mode, chunk, CTAs of one persistent launch)."""
+    out = (ctypes.c_int32 * 3)()
+    rc = load().lbm_get_exec(h, out)
+    if rc:
+        raise LbmError(rc, "lbm_get_exec")
+    return tuple(out[:])
+
+
+def lbm_barrier_selftest(h, limit_ns: int) -> int:
+    flag = ctypes.c_int32()
+    rc = load().lbm_barrier_selftest(h, ctypes.c_uint64(int(limit_ns)), ctypes.byref(flag))
+    if rc:
+        raise LbmError(rc, "lbm_barrier_selftest")
+    return int(flag.value)
+
+
 # ---- convenience owner --------------------------------------------------------
 
 class Lattice:
@@ -317,6 +345,14 @@ class Lattice:
 
     def autotune(self, steps: int = 20):
         return lbm_autotune(self._h, steps)
+
+    def set_exec(self, mode: int, chunk: int = 64):
+        lbm_set_exec(self._h, mode, chunk)
+        return self
+
+    @property
+    def exec(self):
+        return lbm_get_exec(self._h)
 
     @property
     def kernel(self):

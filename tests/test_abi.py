@@ -53,6 +53,8 @@ def test_workspace_size_host_only(lib):
     assert n1 >= 2 * 32 * 256 * 8 * 4
     n2 = lbm.lbm_workspace_size([p, p])
     assert n2 > 1.9 * n1 - 4096
+    p16, _, _ = inputs.sessile(nx=64, ny=48, R=16.0)
+    assert lbm.lbm_workspace_size([p16], lbm.LBM_STORE_FP16) < lbm.lbm_workspace_size([p16])
 
 
 @pytest.mark.parametrize("bad", [dict(nx=2), dict(tau_h=0.5), dict(mobility=0.0),
@@ -67,8 +69,9 @@ def test_invalid_parameters_rejected(lib, bad):
 
 def test_unsupported_storage_rejected(lib):
     p = inputs.params()
-    with pytest.raises(lbm.LbmError):
-        lbm.lbm_workspace_size([p], storage=7)
+    for st in (7, lbm.LBM_STORE_BF16):
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_workspace_size([p], storage=st)
 
 
 def test_error_strings(lib):

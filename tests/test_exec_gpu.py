@@ -1,0 +1,157 @@
+"""Execution forms of lbm_step: per-step launches, CUDA-graph replay, and the
+cooperative persistent kernel with its bounded device-wide barrier.
+
+The graph form replays the very launches the per-step form makes, so its
+states are bitwise identical. The persistent kernel is a separately compiled
+instantiation of the same step body (loads from L2 instead of the read-only
+path), so it agrees to FP32 rounding, as the layout-equivalence tests allow.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2403_16122_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6   # FP32 storage: separately compiled kernels (FMA contraction)
+TOL16 = 2e-5   # FP16 storage: the same, plus a 16-bit rounding that may flip
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2403_16122_gb300 import build
+    from paper_2403_16122_gb300 import lbm as mod
+
+    build.build()
+    mod.load()
+    return mod
+
+
+def _sessile():
+    return inputs.sessile(nx=96, ny=64, R=24.0, theta_deg=100.0)
+
+
+def _run(lbm, cases, mode, chunk, steps, storage=None, kernel=None):
+    storage = lbm.LBM_STORE_FP32 if storage is None else storage
+    lat = lbm.Lattice([c[0] for c in cases], storage=storage)
+    for k, (_, phi0, T0) in enumerate(cases):
+        lat.init(phi0, T0, inst=k)
+    if kernel is not None:
+        lat.set_kernel(*kernel)
+    lat.set_exec(mode, chunk)
+    for n in steps:
+        lat.step(n)
+    obs = lat.observables_all()
+    states = [lat.get_state(k) for k in range(len(cases))]
+    info = (lat.exec, lat.launch_count, lat.step_count)
+    lat.close()
+    return obs, states, info
+
+
+def _max_diff(a, b):
+    return max(max(np.abs(pa - pb).max(), np.abs(xa - xb).max())
+               for (pa, xa), (pb, xb) in zip(a, b))
+
+
+def test_graph_replay_is_bitwise_the_launch_form(lbm):
+    cases = [_sessile()]
+    steps = [37, 64, 1, 50]  # whole chunks, remainders and a single step
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, 16, steps)
+    o2, s2, _ = _run(lbm, cases, lbm.LBM_EXEC_GRAPH, 16, steps)
+    assert _max_diff(s1, s2) == 0.0
+    assert np.array_equal(o1, o2)
+
+
+def test_graph_replay_tile_layout(lbm):
+    cases = [inputs.stefan(nx=128, ny=8, H0=64)]
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, 8, [41], kernel=(lbm.LBM_KERNEL_TILE, 32, 8))
+    o2, s2, _ = _run(lbm, cases, lbm.LBM_EXEC_GRAPH, 8, [41], kernel=(lbm.LBM_KERNEL_TILE, 32, 8))
+    assert _max_diff(s1, s2) == 0.0
+    assert np.array_equal(o1, o2)
+
+
+@pytest.mark.parametrize("chunk", [1, 7, 32])
+def test_persistent_matches_launch_fp32(lbm, chunk):
+    cases = [_sessile()]
+    steps = [100, 3]
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, chunk, steps)
+    o2, s2, info = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, chunk, steps)
+    assert info[0][0] == lbm.LBM_EXEC_PERSISTENT and info[0][2] > 0
+    assert info[2] == 103
+    assert _max_diff(s1, s2) <= TOL32
+    np.testing.assert_allclose(o2, o1, rtol=1e-6, atol=1e-6)
+
+
+def test_persistent_matches_launch_fp16(lbm):
+    cases = [_sessile()]
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, 32, [120], storage=lbm.LBM_STORE_FP16)
+    o2, s2, _ = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, 32, [120], storage=lbm.LBM_STORE_FP16)
+    assert _max_diff(s1, s2) <= TOL16
+    np.testing.assert_allclose(o2, o1, rtol=1e-5, atol=1e-5)
+
+
+def test_persistent_batch_of_uneven_lattices(lbm):
+    """Lattices of different sizes and wetting advance together in one
+    persistent launch; each matches its own per-step-launch trajectory."""
+    cases = inputs.batched_bubbles(n_inst=6, lo=40, hi=90, seed=7)
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, 16, [60])
+    o2, s2, _ = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, 16, [60])
+    assert _max_diff(s1, s2) <= TOL32
+    np.testing.assert_allclose(o2, o1, rtol=1e-6, atol=1e-6)
+
+
+def test_launch_count_of_the_forms(lbm):
+    cases = [_sessile()]
+    # 100 steps with chunk 32: 99 body steps = 3 chunks + 3 steps, then the
+    # observable step and the reduction
+    _, _, (ex, launches, steps) = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, 32, [100])
+    init = 1
+    assert steps == 100
+    assert launches == init + 3 + 1 + 1 + 1
+    _, _, (ex, launches, steps) = _run(lbm, cases, lbm.LBM_EXEC_GRAPH, 32, [100])
+    assert launches == init + 99 + 1 + 1
+
+
+def test_exec_form_validation(lbm):
+    p, phi0, T0 = _sessile()
+    lat = lbm.Lattice([p])
+    lat.init(phi0, T0)
+    for mode, chunk in ((3, 8), (lbm.LBM_EXEC_GRAPH, 0), (lbm.LBM_EXEC_GRAPH, 1 << 17)):
+        with pytest.raises(lbm.LbmError) as e:
+            lat.set_exec(mode, chunk)
+        assert e.value.code == lbm.LBM_EINVAL
+    lat.set_kernel(lbm.LBM_KERNEL_TILE, 32, 8)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.set_exec(lbm.LBM_EXEC_PERSISTENT, 8)  # strip layout only
+    assert e.value.code == lbm.LBM_EINVAL
+    lat.set_kernel(lbm.LBM_KERNEL_STRIP, 4, 16, 168)
+    lat.set_exec(lbm.LBM_EXEC_PERSISTENT, 8)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.set_kernel(lbm.LBM_KERNEL_TILE, 32, 8)
+    assert e.value.code == lbm.LBM_EINVAL
+    assert lat.exec[:2] == (lbm.LBM_EXEC_PERSISTENT, 8)
+    lat.step(20)
+    assert lat.observables()["nonfinite"] == 0
+    lat.close()
+
+
+def test_barrier_wait_expires_and_is_reported(lbm):
+    """A wait at a barrier that no other CTA joins gives up after its time
+    limit and reports it in the error word; the context stays usable."""
+    p, phi0, T0 = _sessile()
+    lat = lbm.Lattice([p])
+    lat.init(phi0, T0)
+    t0 = time.perf_counter()
+    flag = lbm.lbm_barrier_selftest(lat.handle, 20_000_000)  # 20 ms
+    dt = time.perf_counter() - t0
+    assert flag == 1
+    assert dt < 5.0
+    # the handle and the context still work
+    lat.set_exec(lbm.LBM_EXEC_PERSISTENT, 8).step(17)
+    assert lat.observables()["nonfinite"] == 0
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_barrier_selftest(lat.handle, 0)
+    assert e.value.code == lbm.LBM_EINVAL
+    lat.close()
