@@ -45,6 +45,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-steps", type=int, default=10)
+    ap.add_argument("--kernel", default=None,
+                    help="fixed layout 'kind,a,b,c' as lbm_set_kernel takes it (skips the autotuner)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16-storage comparison on the same workload")
     ap.add_argument("--no-batched", action="store_true",
@@ -294,7 +296,9 @@ def run_ours(args, dist: Dist):
     tune = None
     if args.warmup:
         lat.step(args.warmup)
-    if not args.no_autotune:
+    if args.kernel:
+        lat.set_kernel(*[int(v) for v in args.kernel.split(",")])
+    elif not args.no_autotune:
         tune = [float(t) for t in lat.autotune(steps=args.tune_steps)]
     kernel = lat.kernel
     torch.cuda.synchronize()
@@ -410,7 +414,8 @@ def run_ours(args, dist: Dist):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
-            "kernel": {"kind": "strip" if kernel[0] == 1 else "tile", "params": list(kernel[1:]),
+            "kernel": {"kind": {0: "tile", 1: "strip", 2: "staged"}.get(kernel[0], str(kernel[0])),
+                       "params": list(kernel[1:]),
                        "autotune_ms_per_step": tune},
             "clocks": clocks.summary(),
             "observables": {k: obs[k] for k in ("solid", "volume", "nonfinite")},
@@ -472,6 +477,9 @@ def batched_forms(args, dev, peak):
     ms_b = _timed_steps(lat, k)
     ex, kern = lat.exec, lat.kernel
     ob = lat.observables_all(check=False)
+    # the same batch with the steps replayed from a graph of launches
+    lat.set_exec(lbm.LBM_EXEC_GRAPH, chunk).step(chunk + 1)
+    ms_g = _timed_steps(lat, k)
     lat.close()
     # the same lattices, one handle and one launch per lattice and step
     singles = []
@@ -502,6 +510,7 @@ def batched_forms(args, dev, peak):
         "hbm_frac": BYTES_PER_LU_FP32 * sites / (ms_b * 1e-3) / 1e9 / peak,
         "exec": {"mode": "persistent+graph", "chunk": ex[1], "ctas": ex[2]},
         "kernel": list(kern),
+        "graph_of_launches": {"value": sites / (ms_g * 1e-3) / 1e6, "ms_per_step": ms_g},
         "unbatched": {"value": sites / (ms_p * 1e-3) / 1e6, "unit": "MLUPS", "steps": k1,
                       "ms_per_step": ms_p, "what": "one handle per lattice, advanced one lattice after the other, one launch per step"},
         "speedup_vs_unbatched": ms_p / ms_b,

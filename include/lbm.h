@@ -181,10 +181,19 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
                      lattice of the handle periodic in x. a = warps per CTA,
                      c = register budget per thread: (a, c) in {(4,128),
                      (4,168), (4,255), (8,128), (2,128)}.
-   lbm_create picks STRIP (4, 16, 168) when every lattice is periodic in x,
+   LBM_KERNEL_STAGED: the strip layout with every row a lane consumes
+                     copied ahead (cp.async) into a per-warp ring of
+                     shared-memory slots, so that several rows of loads are
+                     in flight while a row is computed. FP32 and FP16
+                     storage; the same (a, c) pairs as STRIP.
+   For both strip layouts b = 0 picks the rows per strip that let one wave
+   of resident warps take every strip of every lattice; lbm_get_kernel
+   reports the rows in effect.
+   lbm_create picks STAGED (4, 0, 168) when every lattice is periodic in x,
    else TILE (32, 8). */
 #define LBM_KERNEL_TILE   0
 #define LBM_KERNEL_STRIP  1
+#define LBM_KERNEL_STAGED 2
 
 /* Select the kernel layout (host tables are rebuilt and uploaded on the
    stream; synchronises it). LBM_EINVAL for an unsupported combination. */

@@ -134,7 +134,8 @@ struct lbm_handle {
     int storage = 0;
     int kind = LBM_KERNEL_TILE;
     int tx = 32, ty = 8;                 // tile shape
-    int warps = 4, rows = 16, regs = 168; // strip layout
+    int warps = 4, rows = 16, regs = 168; // strip layouts (rows: effective)
+    int rows_req = 16;                    // requested rows per item, 0 = one wave
     std::vector<Item> items;
     Item* d_items = nullptr;
     cudaStream_t stream = nullptr;
@@ -206,8 +207,28 @@ void build_tiles(lbm_handle* h) {
 
 // Strip items ordered by (lattice, row segment, strip) so that warps that run
 // together touch neighbouring columns of the same rows.
+bool is_strip(int kind) { return kind == LBM_KERNEL_STRIP || kind == LBM_KERNEL_STAGED; }
+
+// Rows per strip item: as requested, or (0) the fewest that let one wave of
+// resident warps take every item of every lattice at once.
+int item_rows(const lbm_handle* h) {
+    if (h->rows_req > 0) return h->rows_req;
+    long long strip_rows = 0;
+    int max_ny = kMinRows;
+    for (const auto& p : h->params) {
+        strip_rows += (long long)((p.nx + lbmk::kStripW - 1) / lbmk::kStripW) * p.ny;
+        max_ny = std::max(max_ny, p.ny);
+    }
+    const int warps = lbmk::strip_resident_warps(h->kind == LBM_KERNEL_STAGED, h->warps, h->regs,
+                                                 h->storage);
+    if (warps <= 0) return 16;
+    const long long r = (strip_rows + warps - 1) / warps;
+    return (int)std::min<long long>(std::max<long long>(r, kMinRows), max_ny);
+}
+
 void build_items(lbm_handle* h) {
     h->items.clear();
+    h->rows = item_rows(h);
     for (int k = 0; k < h->n_inst; ++k) {
         const lbm_params& p = h->params[k];
         h->inst[k].part_begin = (int)h->items.size();
@@ -235,11 +256,15 @@ void drop_graphs(lbm_handle* h) {
 
 int upload_tables(lbm_handle* h) {
     drop_graphs(h);  // captured launches carry the old item counts
-    if (h->kind == LBM_KERNEL_STRIP) build_items(h); else build_tiles(h);
+    if (h->kind == LBM_KERNEL_STAGED) {
+        cudaError_t e = lbmk::prepare_staged(h->warps, h->regs, h->storage);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (is_strip(h->kind)) build_items(h); else build_tiles(h);
     cudaError_t e = cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(Inst) * h->n_inst,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    if (h->kind == LBM_KERNEL_STRIP)
+    if (is_strip(h->kind))
         e = cudaMemcpyAsync(h->d_items, h->items.data(), sizeof(Item) * h->items.size(),
                             cudaMemcpyHostToDevice, h->stream);
     else
@@ -248,14 +273,18 @@ int upload_tables(lbm_handle* h) {
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(h->stream);  // host tables may change after return
     if (e != cudaSuccess) return cuda_fail(e);
-    h->persist_grid = h->kind == LBM_KERNEL_STRIP
-                          ? lbmk::persistent_grid(h->warps, h->regs, h->storage, (int)h->items.size())
+    h->persist_grid = is_strip(h->kind)
+                          ? lbmk::persistent_grid(h->kind == LBM_KERNEL_STAGED, h->warps, h->regs,
+                                                  h->storage, (int)h->items.size())
                           : 0;
     return LBM_OK;
 }
 
 // One time step through the ordinary kernels (obs != 0: with observable partials).
 cudaError_t enqueue_step(lbm_handle* h, int parity, int obs, cudaStream_t s) {
+    if (h->kind == LBM_KERNEL_STAGED)
+        return lbmk::launch_step_staged(h->warps, h->regs, h->storage, h->d_inst, h->d_items,
+                                        (int)h->items.size(), parity, obs, h->d_part, s);
     return h->kind == LBM_KERNEL_STRIP
                ? lbmk::launch_step_strip(h->warps, h->regs, h->storage, h->d_inst, h->d_items,
                                          (int)h->items.size(), parity, obs, h->d_part, s)
@@ -267,7 +296,8 @@ cudaError_t enqueue_step(lbm_handle* h, int parity, int obs, cudaStream_t s) {
 cudaError_t enqueue_persistent(lbm_handle* h, int parity, int n, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&h->d_sync->bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    return lbmk::launch_step_strip_persistent(h->warps, h->regs, h->storage, h->persist_grid,
+    return lbmk::launch_step_strip_persistent(h->kind == LBM_KERNEL_STAGED, h->warps, h->regs,
+                                              h->storage, h->persist_grid,
                                               h->d_inst, h->d_items, (int)h->items.size(),
                                               parity, n, &h->d_sync->bar, &h->d_sync->err,
                                               kBarrierLimitNs, s);
@@ -369,7 +399,9 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
     for (int k = 0; k < n_inst; ++k) fill_inst(h, k);
     bool all_px = true;
     for (int k = 0; k < n_inst; ++k) all_px = all_px && p[k].periodic_x;
-    h->kind = all_px ? LBM_KERNEL_STRIP : LBM_KERNEL_TILE;
+    // row-staged strips, one wave of items
+    h->kind = all_px ? LBM_KERNEL_STAGED : LBM_KERNEL_TILE;
+    h->rows_req = 0;
     rc = upload_tables(h);
     if (rc != LBM_OK) {
         delete h;
@@ -642,11 +674,12 @@ int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c)
         if (!lbmk::tile_supported(a, b) || h->storage != LBM_STORE_FP32) return LBM_EINVAL;
         if (h->exec == LBM_EXEC_PERSISTENT) return LBM_EINVAL;  // persistent form is strip-only
         h->kind = kind; h->tx = a; h->ty = b;
-    } else if (kind == LBM_KERNEL_STRIP) {
+    } else if (kind == LBM_KERNEL_STRIP || kind == LBM_KERNEL_STAGED) {
         for (int k = 0; k < h->n_inst; ++k)
             if (!h->params[k].periodic_x) return LBM_EINVAL;
-        if (!lbmk::strip_supported(a, c) || b < kMinRows) return LBM_EINVAL;
-        h->kind = kind; h->warps = a; h->rows = b; h->regs = c;
+        if (!lbmk::strip_supported(a, c) || (b != 0 && b < kMinRows)) return LBM_EINVAL;
+        if (kind == LBM_KERNEL_STAGED && !lbmk::staged_supported(a, c, h->storage)) return LBM_EINVAL;
+        h->kind = kind; h->warps = a; h->rows_req = b; h->regs = c;
     } else {
         return LBM_EINVAL;
     }
@@ -658,7 +691,7 @@ int lbm_set_exec(lbm_handle* h, int32_t mode, int32_t chunk) {
     if (!h || chunk < 1 || chunk > kMaxChunk) return LBM_EINVAL;
     if (mode != LBM_EXEC_LAUNCH && mode != LBM_EXEC_GRAPH && mode != LBM_EXEC_PERSISTENT)
         return LBM_EINVAL;
-    if (mode == LBM_EXEC_PERSISTENT && (h->kind != LBM_KERNEL_STRIP || h->persist_grid <= 0))
+    if (mode == LBM_EXEC_PERSISTENT && (!is_strip(h->kind) || h->persist_grid <= 0))
         return LBM_EINVAL;
     drop_graphs(h);
     h->exec = mode;
@@ -693,7 +726,7 @@ int lbm_barrier_selftest(lbm_handle* h, uint64_t limit_ns, int32_t* err_flag) {
 int lbm_get_kernel(const lbm_handle* h, int32_t* out) {
     if (!h || !out) return LBM_EINVAL;
     out[0] = h->kind;
-    if (h->kind == LBM_KERNEL_STRIP) { out[1] = h->warps; out[2] = h->rows; out[3] = h->regs; }
+    if (is_strip(h->kind)) { out[1] = h->warps; out[2] = h->rows; out[3] = h->regs; }
     else { out[1] = h->tx; out[2] = h->ty; out[3] = 0; }
     return LBM_OK;
 }
@@ -706,10 +739,12 @@ int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, in
     bool all_px = true;
     for (int k = 0; k < h->n_inst; ++k) all_px = all_px && h->params[k].periodic_x;
     if (all_px) {
-        const int rows[] = {8, 16, 32};
+        const int rows[] = {0, 8, 16, 32};
         const int var[][2] = {{4, 168}, {4, 128}, {8, 128}, {4, 255}};
         for (int r : rows)
             for (auto& v : var) cands.push_back({LBM_KERNEL_STRIP, v[0], r, v[1]});
+        for (int r : rows)
+            for (auto& v : var) cands.push_back({LBM_KERNEL_STAGED, v[0], r, v[1]});
     }
     if (h->exec != LBM_EXEC_PERSISTENT) {  // the persistent form is strip-only
         cands.push_back({LBM_KERNEL_TILE, 32, 8, 0});

@@ -67,16 +67,30 @@ cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_in
 // Supported strip-kernel variants (warps per CTA, register budget).
 bool strip_supported(int warps, int regs);
 
-// Persistent form of the strip step: grid size (CTAs) of one cooperative
-// launch over n_items items, at most what the device holds resident at once;
-// 0 if the variant is unsupported.
-int persistent_grid(int warps, int regs, int storage, int n_items);
+// Staged strip variants (rows staged through shared memory with cp.async):
+// FP32 and FP16 storage, the same (warps, regs) pairs as the plain strip kernel.
+bool staged_supported(int warps, int regs, int storage);
+// Raise the dynamic shared-memory limit of a staged variant (host call, once
+// before its first launch; not a stream operation).
+cudaError_t prepare_staged(int warps, int regs, int storage);
+cudaError_t launch_step_staged(int warps, int regs, int storage, const Inst* d_inst,
+                               const Item* d_items, int n_items, int parity, int obs,
+                               double* d_partials, cudaStream_t s);
+// Warps of a strip variant (staged != 0: the staged one) resident at once on
+// the device; 0 if unsupported.
+int strip_resident_warps(int staged, int warps, int regs, int storage);
+
+// Persistent form of the strip step (staged != 0: the row-staged body):
+// grid size (CTAs) of one cooperative launch over n_items items, at most what
+// the device holds resident at once; 0 if the variant is unsupported. Also
+// raises the variant's dynamic shared-memory limit (host call).
+int persistent_grid(int staged, int warps, int regs, int storage, int n_items);
 
 // One cooperative launch of `grid` CTAs that advances every item by nsteps
 // steps (no observables) starting from buffer parity0, with a device-wide
 // barrier between steps on *d_bar (must be zero at launch; the caller resets
 // it in the same stream). A barrier wait longer than limit_ns sets *d_err.
-cudaError_t launch_step_strip_persistent(int warps, int regs, int storage, int grid,
+cudaError_t launch_step_strip_persistent(int staged, int warps, int regs, int storage, int grid,
                                          const Inst* d_inst, const Item* d_items, int n_items,
                                          int parity0, int nsteps, unsigned* d_bar, int* d_err,
                                          unsigned long long limit_ns, cudaStream_t s);

@@ -306,14 +306,39 @@ __device__ __forceinline__ float lap_cols(float cL, float cC, float cR, float sL
     return 6.f * (kW1 * t1 + kW2 * t2);
 }
 
+// Pulled populations of one site as site_update reads them: from arrays, or
+// (row-staged FP32 strips) straight from the lane's ring slot at each use, so
+// that they need not stay live in registers across the collision. The slot
+// form applies the anti-bounce-back of h on the links in hmask.
+struct ArrPops {
+    const float *g, *h, *f;
+    __device__ __forceinline__ float G(int i) const { return g[i]; }
+    __device__ __forceinline__ float H(int i) const { return h[i]; }
+    __device__ __forceinline__ float F(int i) const { return f[i]; }
+};
+struct SlotPops {
+    const float* s;  // this lane's column of the slot (planes 32 floats apart)
+    int hmask;       // bit i: h_i arrives through a Dirichlet wall
+    float abb;       // Cp_ref T_w
+    __device__ __forceinline__ float rd(int q) const {
+        return *reinterpret_cast<const volatile float*>(s + q * 32);
+    }
+    __device__ __forceinline__ float G(int i) const { return rd(i); }
+    __device__ __forceinline__ float H(int i) const {
+        const float v = rd(9 + i);
+        return ((hmask >> i) & 1) ? -v + 2.0f * WGT(i) * abb : v;
+    }
+    __device__ __forceinline__ float F(int i) const { return rd(18 + i); }
+};
+
 // Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
 // three collisions (Eqs. 21, 25, 27-28, 30-33) and the store of the
 // post-collision populations and carried fields of one site. The order of
 // every floating-point operation is fixed here, so all kernels built on it
 // produce bit-identical results.
-template <bool OBS, typename ST = float>
+template <bool OBS, typename ST = float, typename Pops = ArrPops>
 __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macro& m,
-                                            const float g[9], const float h[9], const float f[9],
+                                            const Pops& pop,
                                             float phiux_p, float phiuy_p, const Stencil& st,
                                             void* __restrict__ Bv, float* __restrict__ Baux,
                                             int plane, int own, bool on_col, bool on_row,
@@ -331,9 +356,10 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     float mx = 0.f, my = 0.f, fne0 = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        mx += CX(i) * f[i];
-        my += CY(i) * f[i];
-        if (i) fne0 += f[i];
+        const float fi = pop.F(i);
+        mx += CX(i) * fi;
+        my += CY(i) * fi;
+        if (i) fne0 += fi;
     }
     const float inv_rho = 1.f / rho;
     const float usx = (mx + 0.5f * Fx) * inv_rho, usy = (my + 0.5f * Fy) * inv_rho;
@@ -385,21 +411,22 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         // g (Eqs. 21, 24, 25)
         const float geq = w * phi * (1.f + 3.f * cu);
         const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
-        const float gn = g[i] - P.omega_g * (g[i] - geq) + gsrc * Gi;
+        const float gi = pop.G(i), hi = pop.H(i), fi = pop.F(i);
+        const float gn = gi - P.omega_g * (gi - geq) + gsrc * Gi;
         // h (Eqs. 27-28); h_0 carried shifted by -L f_l
         float hn;
         if (i == 0) {
             const float heq0 = m.Hp + dL - TCpref + kW0 * (TCpref - TCp * uu15);
-            hn = (1.f - P.omega_h) * (h[0] + dL) + P.omega_h * heq0;
+            hn = (1.f - P.omega_h) * (hi + dL) + P.omega_h * heq0;
         } else {
             const float heq = w * TCpref + TCp * si;
-            hn = h[i] - P.omega_h * (h[i] - heq);
+            hn = hi - P.omega_h * (hi - heq);
         }
         // f (Eqs. 30-33)
         const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
         const float cF = CX(i) * Ftx + CY(i) * Fty;
         const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
-        const float fn = f[i] - omega_f * (f[i] - feq) + fsrc * Fi;
+        const float fn = fi - omega_f * (fi - feq) + fsrc * Fi;
         if constexpr (sizeof(ST) == 4) {
             float* B = static_cast<float*>(Bv);
             B[i * plane + own] = gn;
@@ -655,7 +682,7 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
             grad_cols(col_sums(mL, cL, pL), col_sums(mC, cC, pC), col_sums(mR, cR, pR),
                       st.gSx, st.gSy);
         }
-        site_update<OBS>(P, l.flags, m, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
+        site_update<OBS>(P, l.flags, m, ArrPops{g, h, f}, phiux_p, phiuy_p, st, B, Baux, l.plane,
                          y * l.pitch + x, x == l.nx / 2, y == l.ny / 2, ob);
     }
     if (OBS) block_reduce_obs<NT>(ob, partials + (long long)T.part * kObs);
@@ -756,11 +783,142 @@ __device__ __forceinline__ float strip_wet_ghost(float a, float b, float outer_a
     return a + tan_w * fabsf(1.5f * d0 - 0.5f * d1);
 }
 
-// One warp advances strip item W by one step (the body of every strip kernel).
-template <bool OBS, typename ST, bool NC>
-__device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const Item& W,
-                                           int parity, double* __restrict__ partials) {
+// ---------------------------------------------------------------------------
+// Row staging: each lane copies, asynchronously and several rows ahead, every
+// value it will consume from a lattice row into its own column of a per-warp
+// ring of shared-memory slots: the 27 populations pulled into its site (for a
+// link that crosses a wall, the site's own opposite population, i.e. the
+// bounce-back source) and the carried fields of its site. A lane reads back
+// only what it copied itself, so no warp or block barrier is involved;
+// cp.async.wait_group orders the copies before the reads.
+// Slot planes (32 lanes of 4 bytes each): 0..26 the pulled populations, 27 f_l,
+// 28 (phi u)_x, 29 (phi u)_y, 30 p, 31 S; FP16 storage adds 32 phi_ref and
+// 33 T_ref, and its planes 0, 9 and 18 hold the FP32 rest populations, the
+// others the aligned 32-bit word that contains the wanted 16-bit value.
+// ---------------------------------------------------------------------------
+template <typename ST>
+__host__ __device__ constexpr int stage_planes() { return sizeof(ST) == 4 ? 32 : 34; }
+template <typename ST>
+__host__ __device__ constexpr int slot_floats() { return stage_planes<ST>() * 32; }
+
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the copies of lattice row r (possibly -1 or ny for periodic y) into
+// `slot` (this lane's column of one ring slot). macro_only: only what the
+// local macroscopic step needs (g, h, f_l, p, S and the references).
+template <typename ST, bool NC>
+__device__ __forceinline__ void stage_row(const LatT<NC>& l, int xc, int xm, int xp, bool py, int r,
+                                          bool macro_only, float* slot) {
     constexpr bool kHalf = sizeof(ST) != 4;
+    const int ny = l.ny;
+    const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
+    const int rr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+    const int ym = rr == 0 ? ny - 1 : rr - 1, yp = rr == ny - 1 ? 0 : rr + 1;
+    const int o0 = rr * l.pitch, om = ym * l.pitch, op = yp * l.pitch;
+    const int own = o0 + xc;
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+        const int set = q / 9, i = q % 9;
+        if (macro_only && set == 2) continue;
+        if (kHalf && i == 0) {  // FP32 rest population (carried planes 7, 8, 9)
+            cp_async4(slot + q * 32, l.Aaux + (7 + set) * l.plane + own);
+            continue;
+        }
+        const int cy = CY(i), cx = CX(i);
+        const bool wall = (cy > 0 && wlo) || (cy < 0 && whi);
+        const int src = wall ? (9 * set + OPP(i)) * l.plane + own
+                             : q * l.plane + (cy > 0 ? om : (cy < 0 ? op : o0)) +
+                                   (cx > 0 ? xm : (cx < 0 ? xp : xc));
+        if constexpr (kHalf) {
+            // planes and rows hold an even number of 16-bit values, so the
+            // aligned word lies inside the row
+            const __half* A16 = reinterpret_cast<const __half*>(l.A);
+            cp_async4(slot + q * 32, reinterpret_cast<const float*>(A16 + (src & ~1)));
+        } else {
+            cp_async4(slot + q * 32, l.A + src);
+        }
+    }
+    cp_async4(slot + 27 * 32, l.Aaux + own);
+    if (!macro_only) {
+        cp_async4(slot + 28 * 32, l.Aaux + l.plane + own);
+        cp_async4(slot + 29 * 32, l.Aaux + 2 * l.plane + own);
+    }
+    cp_async4(slot + 30 * 32, l.Aaux + 3 * l.plane + own);
+    cp_async4(slot + 31 * 32, l.Aaux + 4 * l.plane + own);
+    if constexpr (kHalf) {
+        cp_async4(slot + 32 * 32, l.Aaux + 5 * l.plane + own);
+        cp_async4(slot + 33 * 32, l.Aaux + 6 * l.plane + own);
+    }
+}
+
+// Parities of the source columns (the 16-bit half of each staged word).
+struct ColPar {
+    int c, m, p;  // of x, x - 1, x + 1 (periodic)
+};
+
+// Set `set` of a staged row, decoded as pull_set does: for FP16 storage with
+// the site's own references (g, h) and the source pressures pref (f; the
+// site's own pressure pref[0] on bounced links); for h at a Dirichlet wall
+// row the bounced populations become anti-bounce-back, -h + 2 w_i Cp_ref T_w.
+template <int SET, typename ST = float>
+__device__ __forceinline__ void staged_set(const float* slot, int r, int ny, bool py, int flags,
+                                           float abb, float v[9], const ColPar& par = ColPar{0, 0, 0},
+                                           const Ref& ref = Ref{0.f, 0.f}, float Cpref = 0.f,
+                                           const float* pref = nullptr) {
+    const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
+    if constexpr (sizeof(ST) == 4) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = slot[(9 * SET + i) * 32];
+        if (SET == 1 && !py) {
+            const bool lo = wlo && (flags & kDirYlo), hi = whi && (flags & kDirYhi);
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                if ((CY(i) > 0 && lo) || (CY(i) < 0 && hi)) v[i] = -v[i] + 2.0f * WGT(i) * abb;
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool wall = (CY(i) > 0 && wlo) || (CY(i) < 0 && whi);
+        if (i == 0) {
+            v[i] = slot[(9 * SET) * 32];
+        } else {
+            const unsigned w = __float_as_uint(slot[(9 * SET + i) * 32]);
+            const int odd = wall ? par.c : (CX(i) > 0 ? par.m : (CX(i) < 0 ? par.p : par.c));
+            const float raw = __half2float(__ushort_as_half((unsigned short)(odd ? w >> 16 : w & 0xffffu)));
+            if (SET == 0) v[i] = raw + WGT(i) * ref.phi;
+            if (SET == 1) v[i] = raw + WGT(i) * Cpref * ref.T;
+            if (SET == 2) v[i] = raw * kInvFScale + f_rest(i, wall ? pref[0] : pref[i]);
+        }
+        if (SET == 1 && wall) {
+            const bool dir = (wlo && (flags & kDirYlo)) || (whi && (flags & kDirYhi));
+            if (dir) v[i] = -v[i] + 2.0f * WGT(i) * abb;
+        }
+    }
+}
+
+// One warp advances strip item W by one step (the body of every strip kernel).
+// STG = 0: populations are loaded where they are consumed; STG >= 3: rows are
+// staged through `ring` (STG slots of this warp): while row y is computed,
+// the copies of rows y + 2 .. y + STG - 1 are in flight.
+template <bool OBS, typename ST, bool NC, int STG = 0>
+__device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const Item& W,
+                                           int parity, double* __restrict__ partials,
+                                           float* ring = nullptr) {
+    constexpr bool kHalf = sizeof(ST) != 4;
+    static_assert(STG == 0 || STG >= 3, "staging needs at least three ring slots");
+    // FP32 staging: the collision reads its populations from the ring slot
+    constexpr bool kSlotPops = STG > 0 && !kHalf;
     const int lane = threadIdx.x & 31;
     const Inst& I = insts[W.inst];
     const Phys P = load_phys(I);
@@ -821,6 +979,37 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         note_outer(y);
     };
 
+    // staged rows: ring index j <-> lattice row y0 - 1 + j, j = 0 .. R - 1
+    const int y0 = W.y0;
+    const int R = W.y1 - y0 + 2;
+    const bool has_lo = y0 >= 1 || c.py, has_hi = W.y1 < ny || c.py;
+    float* const my_ring = ring + lane;
+    auto slot = [&](int j) { return my_ring + (j % (STG > 0 ? STG : 1)) * slot_floats<ST>(); };
+    auto issue = [&](int j) {
+        if constexpr (STG > 0) {
+            if (j < R && (j > 0 || has_lo) && (j < R - 1 || has_hi))
+                stage_row<ST>(l, c.xc, c.xm, c.xp, c.py, y0 - 1 + j, j == 0 || j == R - 1, slot(j));
+            cp_async_commit();  // possibly empty: one group per ring index
+        }
+    };
+    const ColPar par{c.xc & 1, c.xm & 1, c.xp & 1};
+    auto slot_ref = [&](const float* sl) {
+        Ref r{0.f, 0.f};
+        if constexpr (kHalf) { r.phi = sl[32 * 32]; r.T = sl[33 * 32]; }
+        return r;
+    };
+    auto row_macro_staged = [&](int j, int y, Macro& m, float& p, float& S, Ref& r) {
+        float gg[9], hh[9];
+        const float* sl = slot(j);
+        r = slot_ref(sl);
+        staged_set<0, ST>(sl, y, ny, c.py, l.flags, abb, gg, par, r, P.Cpref);
+        staged_set<1, ST>(sl, y, ny, c.py, l.flags, abb, hh, par, r, P.Cpref);
+        m = local_macro(P, gg, hh, sl[27 * 32]);
+        p = sl[30 * 32];
+        S = sl[31 * 32];
+        note_outer(y);
+    };
+
     double ob[kObs];
     if (OBS) {
 #pragma unroll
@@ -833,18 +1022,30 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     float tm = 0.f, t0, tp = 0.f;
     Macro mO;
     Ref rO;
-    const int y0 = W.y0;
-    row_macro(y0, mO, p0, S0, rO);
+    if constexpr (STG > 0) {
+#pragma unroll
+        for (int j = 0; j < STG; ++j) issue(j);
+        cp_async_wait<STG - 2>();  // ring indices 0 and 1 have landed
+        row_macro_staged(1, y0, mO, p0, S0, rO);
+    } else {
+        row_macro(y0, mO, p0, S0, rO);
+    }
     ph0 = mO.phi; rh0 = mO.rho; t0 = mO.T;
-    if (y0 >= 1 || c.py) {
+    if (has_lo) {
         Macro mm;
         Ref rr;
-        row_macro(y0 == 0 ? ny - 1 : y0 - 1, mm, pm, Sm, rr);
+        if constexpr (STG > 0) row_macro_staged(0, y0 == 0 ? ny - 1 : y0 - 1, mm, pm, Sm, rr);
+        else row_macro(y0 == 0 ? ny - 1 : y0 - 1, mm, pm, Sm, rr);
         phm = mm.phi; rhm = mm.rho; tm = mm.T;
     }
 
     for (int y = y0; y < W.y1; ++y) {
         const int own = y * l.pitch + c.xc;
+        const int jy = y - y0 + 1;  // ring index of row y
+        if constexpr (STG > 0) {
+            issue(jy + STG - 1);        // into the slot of row y - 1, no longer read
+            cp_async_wait<STG - 2>();   // row y + 1 has landed
+        }
         // Every load that goes to DRAM for this row is issued here, before any
         // of it is consumed: f and (phi u)^{n-1} of row y, then g, h and the
         // carried scalars of row y+1 (inside row_macro).
@@ -864,15 +1065,28 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                     pref[i] = lane_shift(v, -CX(i));                     // source column x - cx
                 }
             }
-            pull_row<2, ST>(l, c, y, abb, f, rO, P.Cpref, P.h0ref, pref);
+            if constexpr (STG > 0)
+                staged_set<2, ST>(slot(jy), y, ny, c.py, l.flags, abb, f, par, rO, P.Cpref, pref);
+            else
+                pull_row<2, ST>(l, c, y, abb, f, rO, P.Cpref, P.h0ref, pref);
         };
-        if constexpr (!kHalf) pull_f();
-        const float phiux_p = ldAux(l, 1, own), phiuy_p = ldAux(l, 2, own);
+        float phiux_p, phiuy_p;
+        if constexpr (STG > 0) {
+            const float* sl = slot(jy);
+            if constexpr (!kHalf && !kSlotPops) pull_f();
+            phiux_p = sl[28 * 32];
+            phiuy_p = sl[29 * 32];
+        } else {
+            if constexpr (!kHalf) pull_f();
+            phiux_p = ldAux(l, 1, own);
+            phiuy_p = ldAux(l, 2, own);
+        }
         Macro mN;
         Ref rN{0.f, 0.f};
         const bool top_wall = !(y + 1 < ny || c.py);
         if (!top_wall) {
-            row_macro(y + 1 == ny ? 0 : y + 1, mN, pp, Sp, rN);
+            if constexpr (STG > 0) row_macro_staged(jy + 1, y + 1 == ny ? 0 : y + 1, mN, pp, Sp, rN);
+            else row_macro(y + 1 == ny ? 0 : y + 1, mN, pp, Sp, rN);
             php = mN.phi; rhp = mN.rho; tp = mN.T;
         } else {
             // row ny lies behind the top wall: ghost from rows ny-1 and ny-2
@@ -923,13 +1137,31 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             }
         }
 
-        if (out_lane) {
+        if constexpr (kSlotPops) {
+            if (out_lane) {
+                int hmask = 0;
+                if (!c.py) {
+                    const bool lo = y == 0 && (l.flags & kDirYlo), hi = y == ny - 1 && (l.flags & kDirYhi);
+#pragma unroll
+                    for (int i = 1; i < 9; ++i)
+                        if ((CY(i) > 0 && lo) || (CY(i) < 0 && hi)) hmask |= 1 << i;
+                }
+                site_update<OBS, ST>(P, l.flags, mO, SlotPops{slot(jy), hmask, abb}, phiux_p,
+                                     phiuy_p, st, B, Baux, l.plane, own, c.xc == nx / 2,
+                                     y == ny / 2, ob, dref);
+            }
+        } else if (out_lane) {
             // g and h of row y were pulled one row earlier: these loads hit L1
             float g[9], h[9];
-            pull_row<0, ST>(l, c, y, abb, g, rO, P.Cpref, P.h0ref);
-            pull_row<1, ST>(l, c, y, abb, h, rO, P.Cpref, P.h0ref);
-            site_update<OBS, ST>(P, l.flags, mO, g, h, f, phiux_p, phiuy_p, st, B, Baux, l.plane,
-                                 own, c.xc == nx / 2, y == ny / 2, ob, dref);
+            if constexpr (STG > 0) {
+                staged_set<0, ST>(slot(jy), y, ny, c.py, l.flags, abb, g, par, rO, P.Cpref);
+                staged_set<1, ST>(slot(jy), y, ny, c.py, l.flags, abb, h, par, rO, P.Cpref);
+            } else {
+                pull_row<0, ST>(l, c, y, abb, g, rO, P.Cpref, P.h0ref);
+                pull_row<1, ST>(l, c, y, abb, h, rO, P.Cpref, P.h0ref);
+            }
+            site_update<OBS, ST>(P, l.flags, mO, ArrPops{g, h, f}, phiux_p, phiuy_p, st, B, Baux,
+                                 l.plane, own, c.xc == nx / 2, y == ny / 2, ob, dref);
         }
 
         // advance the window
@@ -939,6 +1171,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         mO = mN;
         rO = rN;
     }
+    if constexpr (STG > 0) cp_async_wait<0>();  // the trailing groups are empty
 
     if (OBS) {
 #pragma unroll
@@ -961,6 +1194,26 @@ step_strip(const Inst* __restrict__ insts, const Item* __restrict__ items, int n
     const int it = blockIdx.x * WARPS + (threadIdx.x >> 5);
     if (it >= n_items) return;  // whole warp leaves together; no block barrier in the body
     strip_item<OBS, ST, true>(insts, items[it], parity, partials);
+}
+
+// Staged form: STG ring slots of slot_floats<ST>() floats per warp in dynamic
+// shared memory.
+template <int WARPS, int MINB, int STG, bool OBS, typename ST>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+step_strip_staged(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
+                  int parity, double* __restrict__ partials) {
+    extern __shared__ float ring_smem[];
+    // Programmatic dependent launch: let the next step's grid be scheduled as
+    // soon as every CTA of this one has started, and touch no lattice data
+    // before the previous step's grid has completed (a no-op when launched
+    // without the attribute).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int warp = threadIdx.x >> 5;
+    const int it = blockIdx.x * WARPS + warp;
+    if (it >= n_items) return;  // whole warp leaves together; no block barrier in the body
+    strip_item<OBS, ST, true, STG>(insts, items[it], parity, partials,
+                                   ring_smem + warp * (STG * slot_floats<ST>()));
 }
 
 // Device-wide barrier between the steps of the persistent kernel. Every CTA
@@ -1007,18 +1260,24 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
 // Persistent form: one cooperative launch advances every item of every
 // lattice by `nsteps` steps (parity alternating from parity0), each warp
 // taking items in grid-stride order, with a device-wide barrier between
-// steps. *bar must be zero at launch.
-template <int WARPS, int MINB, typename ST>
+// steps. *bar must be zero at launch. STG > 0: the row-staged body, with
+// STG ring slots per warp in dynamic shared memory. The staged rows are
+// copied through L1 (cp.async of 4 bytes has no L2-only form); they were
+// written by other CTAs before the barrier, whose acquire orders these
+// copies after those writes.
+template <int WARPS, int MINB, int STG, typename ST>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
 step_strip_persistent(const Inst* __restrict__ insts, const Item* __restrict__ items,
                       int n_items, int parity0, int nsteps, unsigned* bar, int* err,
                       unsigned long long limit_ns) {
+    extern __shared__ float ring_smem[];
+    float* ring = ring_smem + (threadIdx.x >> 5) * (STG * slot_floats<ST>());
     const int warp = blockIdx.x * WARPS + (threadIdx.x >> 5);
     const int stride = gridDim.x * WARPS;
     for (int s = 0; s < nsteps; ++s) {
         const int parity = parity0 ^ (s & 1);
         for (int it = warp; it < n_items; it += stride)
-            strip_item<false, ST, false>(insts, items[it], parity, nullptr);
+            strip_item<false, ST, false, STG>(insts, items[it], parity, nullptr, ring);
         if (s + 1 < nsteps &&
             !grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, err, limit_ns))
             return;
@@ -1198,17 +1457,87 @@ cudaError_t launch_strip_w(const Inst* d_inst, const Item* d_items, int n_items,
     return cudaGetLastError();
 }
 
+// Staged launches: ring depth and dynamic shared memory of a variant.
+template <int WARPS, int MINB, int STG, typename ST>
+struct Staged {
+    static constexpr int kSmem = WARPS * STG * slot_floats<ST>() * (int)sizeof(float);
+    static cudaError_t prepare() {
+        cudaError_t e = cudaFuncSetAttribute(step_strip_staged<WARPS, MINB, STG, false, ST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_strip_staged<WARPS, MINB, STG, true, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        return e;
+    }
+    static int resident_warps() {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, step_strip_staged<WARPS, MINB, STG, false, ST>, WARPS * 32, kSmem) != cudaSuccess)
+            return 0;
+        return per_sm * sms * WARPS;
+    }
+    static cudaError_t launch(const Inst* d_inst, const Item* d_items, int n_items, int parity,
+                              int obs, double* d_partials, cudaStream_t s) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((n_items + WARPS - 1) / WARPS);
+        cfg.blockDim = dim3(WARPS * 32);
+        cfg.dynamicSmemBytes = kSmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (obs)
+            return cudaLaunchKernelEx(&cfg, step_strip_staged<WARPS, MINB, STG, true, ST>, d_inst,
+                                      d_items, n_items, parity, d_partials);
+        return cudaLaunchKernelEx(&cfg, step_strip_staged<WARPS, MINB, STG, false, ST>, d_inst,
+                                  d_items, n_items, parity, d_partials);
+    }
+};
+
+// Dispatch over the supported staged variants (warps per CTA, register
+// budget): the ring depth follows from what the register budget leaves
+// resident per SM, keeping every variant's shared memory within ~210 KB/SM.
+template <typename ST, typename F>
+auto staged_dispatch(int warps, int regs, F&& f) -> decltype(f(Staged<4, 3, 4, ST>())) {
+    if (warps == 4 && regs == 128) return f(Staged<4, 4, 3, ST>());
+    if (warps == 4 && regs == 255) return f(Staged<4, 2, 5, ST>());
+    if (warps == 8 && regs == 128) return f(Staged<8, 2, 3, ST>());
+    if (warps == 2 && regs == 128) return f(Staged<2, 8, 3, ST>());
+    return f(Staged<4, 3, 4, ST>());
+}
+
+// Warps resident at once for a plain strip variant.
+template <int WARPS, int MINB, typename ST>
+int plain_resident_warps() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_strip<WARPS, MINB, false, ST>,
+                                                      WARPS * 32, 0) != cudaSuccess)
+        return 0;
+    return per_sm * sms * WARPS;
+}
+
 // Persistent launches: the kernel of a (warps, regs, storage) variant, and
 // the co-resident grid for it.
-template <int WARPS, int MINB, typename ST>
+template <int WARPS, int MINB, int STG, typename ST>
 struct Persist {
-    static void* fn() { return reinterpret_cast<void*>(&step_strip_persistent<WARPS, MINB, ST>); }
+    static constexpr int kSmem = WARPS * STG * slot_floats<ST>() * (int)sizeof(float);
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(step_strip_persistent<WARPS, MINB, STG, ST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    }
     static int grid(int n_items) {
         int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_strip_persistent<WARPS, MINB, ST>,
-                                                          WARPS * 32, 0) != cudaSuccess)
+        if (prepare() != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, step_strip_persistent<WARPS, MINB, STG, ST>, WARPS * 32, kSmem) != cudaSuccess)
             return 0;
         const int want = (n_items + WARPS - 1) / WARPS;
         return std::max(1, std::min(want, per_sm * sms));
@@ -1219,26 +1548,34 @@ struct Persist {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(WARPS * 32);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = kSmem;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, step_strip_persistent<WARPS, MINB, ST>, d_inst, d_items,
-                                  n_items, parity0, nsteps, bar, err, limit_ns);
+        return cudaLaunchKernelEx(&cfg, step_strip_persistent<WARPS, MINB, STG, ST>, d_inst,
+                                  d_items, n_items, parity0, nsteps, bar, err, limit_ns);
     }
 };
 
-// Dispatch of a persistent call F over the supported strip variants.
+// Dispatch of a persistent call F over the supported strip variants, plain
+// (staged == 0) or row-staged with the ring depths of the staged kernels.
 template <typename ST, typename F>
-auto persist_dispatch(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, ST>())) {
-    if (warps == 4 && regs == 128) return f(Persist<4, 4, ST>());
-    if (warps == 4 && regs == 168) return f(Persist<4, 3, ST>());
-    if (warps == 4 && regs == 255) return f(Persist<4, 1, ST>());
-    if (warps == 8 && regs == 128) return f(Persist<8, 2, ST>());
-    return f(Persist<2, 8, ST>());
+auto persist_dispatch(int staged, int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 0, ST>())) {
+    if (staged) {
+        if (warps == 4 && regs == 128) return f(Persist<4, 4, 3, ST>());
+        if (warps == 4 && regs == 255) return f(Persist<4, 2, 5, ST>());
+        if (warps == 8 && regs == 128) return f(Persist<8, 2, 3, ST>());
+        if (warps == 2 && regs == 128) return f(Persist<2, 8, 3, ST>());
+        return f(Persist<4, 3, 4, ST>());
+    }
+    if (warps == 4 && regs == 128) return f(Persist<4, 4, 0, ST>());
+    if (warps == 4 && regs == 168) return f(Persist<4, 3, 0, ST>());
+    if (warps == 4 && regs == 255) return f(Persist<4, 1, 0, ST>());
+    if (warps == 8 && regs == 128) return f(Persist<8, 2, 0, ST>());
+    return f(Persist<2, 8, 0, ST>());
 }
 
 template <typename ST>
@@ -1266,14 +1603,54 @@ cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_in
     return launch_strip_st<float>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials, s);
 }
 
-int persistent_grid(int warps, int regs, int storage, int n_items) {
-    if (!strip_supported(warps, regs) || n_items <= 0) return 0;
-    auto g = [&](auto v) { return decltype(v)::grid(n_items); };
-    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(warps, regs, g);
-    return persist_dispatch<float>(warps, regs, g);
+bool staged_supported(int warps, int regs, int storage) {
+    return (storage == LBM_STORE_FP32 || storage == LBM_STORE_FP16) && strip_supported(warps, regs);
 }
 
-cudaError_t launch_step_strip_persistent(int warps, int regs, int storage, int grid,
+cudaError_t prepare_staged(int warps, int regs, int storage) {
+    auto go = [](auto v) { return decltype(v)::prepare(); };
+    return storage == LBM_STORE_FP16 ? staged_dispatch<__half>(warps, regs, go)
+                                     : staged_dispatch<float>(warps, regs, go);
+}
+
+cudaError_t launch_step_staged(int warps, int regs, int storage, const Inst* d_inst,
+                               const Item* d_items, int n_items, int parity, int obs,
+                               double* d_partials, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (!staged_supported(warps, regs, storage)) return cudaErrorInvalidValue;
+    auto go = [&](auto v) {
+        return decltype(v)::launch(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    };
+    return storage == LBM_STORE_FP16 ? staged_dispatch<__half>(warps, regs, go)
+                                     : staged_dispatch<float>(warps, regs, go);
+}
+
+int strip_resident_warps(int staged, int warps, int regs, int storage) {
+    if (!strip_supported(warps, regs)) return 0;
+    if (staged) {
+        auto go = [](auto v) { return decltype(v)::resident_warps(); };
+        return storage == LBM_STORE_FP16 ? staged_dispatch<__half>(warps, regs, go)
+                                         : staged_dispatch<float>(warps, regs, go);
+    }
+    auto pick = [&](auto tag) -> int {
+        using ST = decltype(tag);
+        if (warps == 4 && regs == 128) return plain_resident_warps<4, 4, ST>();
+        if (warps == 4 && regs == 255) return plain_resident_warps<4, 1, ST>();
+        if (warps == 8 && regs == 128) return plain_resident_warps<8, 2, ST>();
+        if (warps == 2 && regs == 128) return plain_resident_warps<2, 8, ST>();
+        return plain_resident_warps<4, 3, ST>();
+    };
+    return storage == LBM_STORE_FP16 ? pick(__half()) : pick(float());
+}
+
+int persistent_grid(int staged, int warps, int regs, int storage, int n_items) {
+    if (!strip_supported(warps, regs) || n_items <= 0) return 0;
+    auto g = [&](auto v) { return decltype(v)::grid(n_items); };
+    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(staged, warps, regs, g);
+    return persist_dispatch<float>(staged, warps, regs, g);
+}
+
+cudaError_t launch_step_strip_persistent(int staged, int warps, int regs, int storage, int grid,
                                          const Inst* d_inst, const Item* d_items, int n_items,
                                          int parity0, int nsteps, unsigned* d_bar, int* d_err,
                                          unsigned long long limit_ns, cudaStream_t s) {
@@ -1283,9 +1660,9 @@ cudaError_t launch_step_strip_persistent(int warps, int regs, int storage, int g
         return decltype(v)::launch(grid, d_inst, d_items, n_items, parity0, nsteps, d_bar, d_err,
                                    limit_ns, s);
     };
-    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(warps, regs, go);
+    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(staged, warps, regs, go);
     if (storage != LBM_STORE_FP32) return cudaErrorNotSupported;
-    return persist_dispatch<float>(warps, regs, go);
+    return persist_dispatch<float>(staged, warps, regs, go);
 }
 
 cudaError_t launch_barrier_timeout_probe(unsigned* d_bar, int* d_err, unsigned long long limit_ns,

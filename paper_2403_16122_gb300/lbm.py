@@ -65,7 +65,7 @@ SYMBOLS = (
     "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune", "lbm_step_noalloc",
     "lbm_set_exec", "lbm_get_exec", "lbm_barrier_selftest",
 )
-LBM_KERNEL_TILE, LBM_KERNEL_STRIP = 0, 1
+LBM_KERNEL_TILE, LBM_KERNEL_STRIP, LBM_KERNEL_STAGED = 0, 1, 2
 LBM_EXEC_LAUNCH, LBM_EXEC_GRAPH, LBM_EXEC_PERSISTENT = 0, 1, 2
 
 

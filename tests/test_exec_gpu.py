@@ -3,7 +3,7 @@ cooperative persistent kernel with its bounded device-wide barrier.
 
 The graph form replays the very launches the per-step form makes, so its
 states are bitwise identical. The persistent kernel is a separately compiled
-instantiation of the same step body (loads from L2 instead of the read-only
+instantiation of the same step body (coherent loads instead of the read-only
 path), so it agrees to FP32 rounding, as the layout-equivalence tests allow.
 """
 import time
@@ -72,22 +72,30 @@ def test_graph_replay_tile_layout(lbm):
     assert np.array_equal(o1, o2)
 
 
-@pytest.mark.parametrize("chunk", [1, 7, 32])
-def test_persistent_matches_launch_fp32(lbm, chunk):
+@pytest.mark.parametrize("chunk,kind", [(1, 2), (7, 2), (32, 2), (7, 1), (32, 1)])
+def test_persistent_matches_launch_fp32(lbm, chunk, kind):
+    """Both strip bodies (plain: L2 loads; staged: rows copied through L1
+    after the barrier's acquire) on a lattice small enough to stay in L1,
+    where a stale line would show at once."""
     cases = [_sessile()]
     steps = [100, 3]
-    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, chunk, steps)
-    o2, s2, info = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, chunk, steps)
+    kern = (kind, 4, 0, 168)
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, chunk, steps, kernel=kern)
+    o2, s2, info = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, chunk, steps, kernel=kern)
     assert info[0][0] == lbm.LBM_EXEC_PERSISTENT and info[0][2] > 0
     assert info[2] == 103
     assert _max_diff(s1, s2) <= TOL32
     np.testing.assert_allclose(o2, o1, rtol=1e-6, atol=1e-6)
 
 
-def test_persistent_matches_launch_fp16(lbm):
+@pytest.mark.parametrize("kind", [1, 2])
+def test_persistent_matches_launch_fp16(lbm, kind):
     cases = [_sessile()]
-    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, 32, [120], storage=lbm.LBM_STORE_FP16)
-    o2, s2, _ = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, 32, [120], storage=lbm.LBM_STORE_FP16)
+    kern = (kind, 4, 0, 168)
+    o1, s1, _ = _run(lbm, cases, lbm.LBM_EXEC_LAUNCH, 32, [120], storage=lbm.LBM_STORE_FP16,
+                     kernel=kern)
+    o2, s2, _ = _run(lbm, cases, lbm.LBM_EXEC_PERSISTENT, 32, [120], storage=lbm.LBM_STORE_FP16,
+                     kernel=kern)
     assert _max_diff(s1, s2) <= TOL16
     np.testing.assert_allclose(o2, o1, rtol=1e-5, atol=1e-5)
 

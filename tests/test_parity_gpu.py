@@ -181,16 +181,19 @@ def test_step_zero_and_call_order():
     assert lat.step_count == 3
 
 
-STRIP_VARIANTS = [(4, 16, 168), (4, 8, 128), (8, 32, 128), (2, 2, 128), (4, 16, 255)]
+STRIP_VARIANTS = [(1, 4, 16, 168), (1, 4, 8, 128), (1, 8, 32, 128), (1, 2, 2, 128),
+                  (1, 4, 16, 255), (1, 4, 0, 168),
+                  (2, 4, 16, 168), (2, 4, 3, 128), (2, 8, 32, 128), (2, 2, 2, 128),
+                  (2, 4, 5, 255), (2, 4, 0, 168)]
 
 
 @pytest.mark.parametrize("case", ["sessile", "bubbles", "tiny", "narrow_walls", "periodic"])
 def test_strip_kernel_matches_tile_kernel(case):
-    """The warp-strip layout and the shared-memory tile layout run the same
-    per-site code (the compiler may contract multiply-adds differently per
-    kernel instantiation, so they agree to FP32 rounding rather than bit for
-    bit): within 1e-6 after 60 steps for every strip variant (segment lengths
-    down to 2 rows)."""
+    """The warp-strip layouts (plain and row-staged) and the shared-memory
+    tile layout run the same per-site code (the compiler may contract
+    multiply-adds differently per kernel instantiation, so they agree to FP32
+    rounding rather than bit for bit): within 1e-6 after 60 steps for every
+    strip variant (segment lengths down to 2 rows, and the one-wave choice)."""
     from paper_2403_16122_gb300 import lbm
 
     if case == "sessile":
@@ -213,8 +216,10 @@ def test_strip_kernel_matches_tile_kernel(case):
     want_obs = ref.observables()
     for v in STRIP_VARIANTS:
         lat = gpu_run([p], [(phi0, T0)], 0)
-        lat.set_kernel(lbm.LBM_KERNEL_STRIP, *v)
-        assert lat.kernel == (lbm.LBM_KERNEL_STRIP, *v)
+        lat.set_kernel(*v)
+        kind, warps, rows, regs = lat.kernel
+        assert (kind, warps, regs) == (v[0], v[1], v[3]) and rows >= 2
+        assert v[2] == 0 or rows == v[2]
         lat.step(60)
         got = lat.get_state()
         assert np.abs(got[0] - want[0]).max() <= 1e-6, v
@@ -236,7 +241,8 @@ def test_kernel_selection_and_autotune():
         lat.set_kernel(lbm.LBM_KERNEL_TILE, 33, 8)
     p, phi0, T0 = inputs.sessile(nx=96, ny=64, R=20.0)
     a = gpu_run([p], [(phi0, T0)], 0)
-    assert a.kernel == (lbm.LBM_KERNEL_STRIP, 4, 16, 168)
+    kind, warps, rows, regs = a.kernel  # staged strips, one wave of items
+    assert (kind, warps, regs) == (lbm.LBM_KERNEL_STAGED, 4, 168) and rows >= 2
     times = a.autotune(steps=3)
     assert len(times) >= 4 and np.all(times > 0)
     n = a.step_count
