@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--tune-steps", type=int, default=10)
     ap.add_argument("--kernel", default=None,
                     help="fixed layout 'kind,a,b,c' as lbm_set_kernel takes it (skips the autotuner)")
+    ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",
+                    help="storage of the main timed lattice (the metric is quoted on fp32)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16-storage comparison on the same workload")
     ap.add_argument("--no-batched", action="store_true",
@@ -194,7 +196,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(workload: str):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"step_fp32_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"step_{workload}.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -287,7 +289,10 @@ def run_ours(args, dist: Dist):
     n = args.n
     p, phi0, T0 = inputs.bubbles_drop(n=n)
     sites = n * n
-    lat = lbm.Lattice([p], device=dev)
+    fp16 = args.storage == "fp16"
+    bytes_lu = BYTES_PER_LU_FP16 if fp16 else BYTES_PER_LU_FP32
+    workload = WORKLOAD.replace("fp32", "fp16") if fp16 else WORKLOAD
+    lat = lbm.Lattice([p], storage=lbm.LBM_STORE_FP16 if fp16 else lbm.LBM_STORE_FP32, device=dev)
     stream = lat.stream
     lat.init(phi0, T0)
 
@@ -325,12 +330,12 @@ def run_ours(args, dist: Dist):
 
     # roofline of the dominant kernel (the fused step), from the same events
     peak, peak_kind = measured_hbm_peak()
-    achieved = BYTES_PER_LU_FP32 * sites / (ms / args.steps * 1e-3) / 1e9
-    traffic = profiled_traffic(WORKLOAD)
+    achieved = bytes_lu * sites / (ms / args.steps * 1e-3) / 1e9
+    traffic = profiled_traffic(workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": BYTES_PER_LU_FP32 * sites}
+                "algorithmic_bytes_per_launch": bytes_lu * sites}
 
     # end to end through the C-ABI with host buffers: upload the fields from
     # pinned memory, then per step one time step and a read of the observables
@@ -405,10 +410,10 @@ def run_ours(args, dist: Dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": n, "ny": n, "sites": sites,
-                       "storage": "fp32", "bubbles": 8, "parallelism": f"replicas{dist.world}",
+            "config": {"workload": workload, "nx": n, "ny": n, "sites": sites,
+                       "storage": args.storage, "bubbles": 8, "parallelism": f"replicas{dist.world}",
                        "l2": "inputs larger than L2 (268 MB moved per step)",
-                       "bytes_per_lu": BYTES_PER_LU_FP32},
+                       "bytes_per_lu": bytes_lu},
             "roofline": roofline,
             "forms": forms,
             "cpu_baseline": cpu,

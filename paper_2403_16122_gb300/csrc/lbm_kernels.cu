@@ -437,27 +437,28 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                 g0n = gn; h0n = hn; f0n = fn;
             } else {
                 // deviations from the rest equilibria (g, h: destination's
-                // references dref[i]; f: this site's pressure), and the error
-                // the destination will see after decoding
+                // references dref[i]; f: this site's pressure), and what their
+                // rounding to 16 bits takes away from what the site sends
                 __half* B = static_cast<__half*>(Bv);
                 const Ref& d = dref[i];
-                const float rg = w * d.phi, rh = w * P.Cpref * d.T, rf = f_rest(i, pn);
-                const __half qg = __float2half_rn(gn - rg);
-                const __half qh = __float2half_rn(hn - rh);
-                const __half qf = __float2half_rn((fn - rf) * kFScale);
+                const float dg = gn - w * d.phi, dh = hn - w * P.Cpref * d.T;
+                const float df = (fn - f_rest(i, pn)) * kFScale;
+                const __half qg = __float2half_rn(dg);
+                const __half qh = __float2half_rn(dh);
+                const __half qf = __float2half_rn(df);
                 B[i * plane + own] = qg;
                 B[(9 + i) * plane + own] = qh;
                 B[(18 + i) * plane + own] = qf;
-                eg += (__half2float(qg) + rg) - gn;
-                eh += (__half2float(qh) + rh) - hn;
-                ef += (__half2float(qf) * kInvFScale + rf) - fn;
+                eg += dg - __half2float(qg);
+                eh += dh - __half2float(qh);
+                ef += df - __half2float(qf);
             }
         }
     }
-    if constexpr (sizeof(ST) != 4) {
-        Baux[7 * plane + own] = g0n - eg;
-        Baux[8 * plane + own] = h0n - eh;
-        Baux[9 * plane + own] = f0n - ef;
+    if constexpr (sizeof(ST) != 4) {  // the rest populations carry the rounding
+        Baux[7 * plane + own] = g0n + eg;
+        Baux[8 * plane + own] = h0n + eh;
+        Baux[9 * plane + own] = f0n + ef * kInvFScale;
     }
     Baux[own] = m.fl;
     Baux[plane + own] = phiux;
@@ -861,10 +862,13 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int xc, int xm, int
     }
 }
 
-// Parities of the source columns (the 16-bit half of each staged word).
+// Which 16-bit half of each staged word a lane wants, as __byte_perm
+// selectors for the source columns x, x - 1 and x + 1 (periodic): 0x3232 the
+// upper half (odd column), 0x1010 the lower half.
 struct ColPar {
-    int c, m, p;  // of x, x - 1, x + 1 (periodic)
+    unsigned c, m, p;
 };
+__device__ __forceinline__ unsigned half_sel(int col) { return (col & 1) ? 0x3232u : 0x1010u; }
 
 // Set `set` of a staged row, decoded as pull_set does: for FP16 storage with
 // the site's own references (g, h) and the source pressures pref (f; the
@@ -894,8 +898,8 @@ __device__ __forceinline__ void staged_set(const float* slot, int r, int ny, boo
             v[i] = slot[(9 * SET) * 32];
         } else {
             const unsigned w = __float_as_uint(slot[(9 * SET + i) * 32]);
-            const int odd = wall ? par.c : (CX(i) > 0 ? par.m : (CX(i) < 0 ? par.p : par.c));
-            const float raw = __half2float(__ushort_as_half((unsigned short)(odd ? w >> 16 : w & 0xffffu)));
+            const unsigned sel = wall ? par.c : (CX(i) > 0 ? par.m : (CX(i) < 0 ? par.p : par.c));
+            const float raw = __half2float(__ushort_as_half((unsigned short)__byte_perm(w, 0u, sel)));
             if (SET == 0) v[i] = raw + WGT(i) * ref.phi;
             if (SET == 1) v[i] = raw + WGT(i) * Cpref * ref.T;
             if (SET == 2) v[i] = raw * kInvFScale + f_rest(i, wall ? pref[0] : pref[i]);
@@ -917,8 +921,9 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                                            float* ring = nullptr) {
     constexpr bool kHalf = sizeof(ST) != 4;
     static_assert(STG == 0 || STG >= 3, "staging needs at least three ring slots");
-    // FP32 staging: the collision reads its populations from the ring slot
-    constexpr bool kSlotPops = STG > 0 && !kHalf;
+    // Staging: the collision reads its populations from the ring slot (FP16:
+    // the decoded values, written back over the staged words)
+    constexpr bool kSlotPops = STG > 0;
     const int lane = threadIdx.x & 31;
     const Inst& I = insts[W.inst];
     const Phys P = load_phys(I);
@@ -992,7 +997,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             cp_async_commit();  // possibly empty: one group per ring index
         }
     };
-    const ColPar par{c.xc & 1, c.xm & 1, c.xp & 1};
+    const ColPar par{half_sel(c.xc), half_sel(c.xm), half_sel(c.xp)};
     auto slot_ref = [&](const float* sl) {
         Ref r{0.f, 0.f};
         if constexpr (kHalf) { r.phi = sl[32 * 32]; r.T = sl[33 * 32]; }
@@ -1004,6 +1009,11 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         r = slot_ref(sl);
         staged_set<0, ST>(sl, y, ny, c.py, l.flags, abb, gg, par, r, P.Cpref);
         staged_set<1, ST>(sl, y, ny, c.py, l.flags, abb, hh, par, r, P.Cpref);
+        if constexpr (kHalf) {  // keep the decoded values for the collision
+            float* ws = const_cast<float*>(sl);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) { ws[i * 32] = gg[i]; ws[(9 + i) * 32] = hh[i]; }
+        }
         m = local_macro(P, gg, hh, sl[27 * 32]);
         p = sl[30 * 32];
         S = sl[31 * 32];
@@ -1099,7 +1109,14 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             phm = strip_wet_ghost(ph0, php, oB0, oB1, lane, P.tan_w);
             rhm = rh0; pm = p0; Sm = S0; tm = t0;
         }
-        if constexpr (kHalf) pull_f();
+        if constexpr (kHalf) {
+            pull_f();
+            if constexpr (STG > 0) {  // decoded f for the collision's slot reads
+                float* ws = slot(jy);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) ws[(18 + i) * 32] = f[i];
+            }
+        }
 
         // Eq. 38 from column sums exchanged with the neighbouring lanes
         Stencil st;
@@ -1139,8 +1156,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
 
         if constexpr (kSlotPops) {
             if (out_lane) {
-                int hmask = 0;
-                if (!c.py) {
+                int hmask = 0;  // FP16: applied when the slot was decoded
+                if (!kHalf && !c.py) {
                     const bool lo = y == 0 && (l.flags & kDirYlo), hi = y == ny - 1 && (l.flags & kDirYhi);
 #pragma unroll
                     for (int i = 1; i < 9; ++i)

@@ -33,7 +33,8 @@ def test_fp16_observables_match_oracle(oracle_mod, case):
     h16 = gpu_run([p], [(phi0, T0)], steps, storage=lbm.LBM_STORE_FP16)
     o = oracle_run(oracle_mod, p, phi0, T0, steps)
     g, r = h16.observables(), o.observables()
-    print(case, {k: (g[k], r[k]) for k in ("volume", "solid", "solid_col")})
+    f = gpu_run([p], [(phi0, T0)], steps).observables()
+    print(case, {k: (g[k], f[k], r[k]) for k in ("volume", "solid", "solid_col", "enthalpy")})
     assert r["solid"] > 5.0
     assert g["volume"] == pytest.approx(r["volume"], rel=0.01)
     assert g["solid"] == pytest.approx(r["solid"], rel=0.01)
@@ -149,6 +150,7 @@ def test_fp16_batched_freezing_time_within_one_percent():
     checked = 0
     for thr in (0.5, 0.9):
         t32, t16 = _crossing_times(t, X32, thr), _crossing_times(t, X16, thr)
+        print("X =", thr, "t32", np.round(t32, 1), "t16", np.round(t16, 1))
         for a, b in zip(t32, t16):
             if np.isnan(a):
                 continue
