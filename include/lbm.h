@@ -272,13 +272,15 @@ int64_t lbm_launch_count(const lbm_handle* h);
    (out) and writes the observables record of that step, and it calls no
    cudaMalloc, cudaFree or other allocating routine.
 
-   Buffers (device, caller-owned, FP32, 16-byte aligned): pops_in/pops_out hold
-   27 planes of ny rows of `pitch` floats (pitch >= nx) in the order g_0..g_8,
-   h_0..h_8, f_0..f_8, with h_0 stored shifted by -L f_l (L = Cp (T_m - T_w) /
-   Ste, f_l the first aux plane of the same buffer); aux_in/aux_out hold the
-   five carried planes f_l, (phi u)_x, (phi u)_y, p, S with the same pitch.
-   This is exactly the layout of a handle's state buffers. in and out must not
-   overlap. d_obs receives LBM_OBS_COUNT doubles (device memory).
+   Buffers (device, caller-owned, FP32, 16-byte aligned), in the library's
+   grouped state layout with site = y * pitch + x (pitch >= nx) and
+   plane = pitch * ny: pops_in/pops_out hold 24 * plane floats, the pair
+   (g_i, h_i) of direction i = 1..8 at 2 (i - 1) plane + 2 site and f_i at
+   (15 + i) plane + site; aux_in/aux_out hold 8 * plane floats, the group
+   (g_0, h_0 - L f_l, f_0, f_l) at 4 site and ((phi u)_x, (phi u)_y, p, S) at
+   4 plane + 4 site (L = Cp (T_m - T_w) / Ste). This is exactly the layout of
+   a handle's FP32 state buffers. in and out must not overlap. d_obs receives
+   LBM_OBS_COUNT doubles (device memory).
 
    Scratch: the per-tile partial sums of the observables live in one array of
    LBM_NOALLOC_MAX_TILES * LBM_OBS_COUNT doubles (720 KiB) that is part of the

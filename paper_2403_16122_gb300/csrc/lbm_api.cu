@@ -53,9 +53,12 @@ bool valid_params(const lbm_params& p) {
 }
 
 int elem_size(int storage) { return storage == LBM_STORE_FP32 ? 4 : 2; }
-// carried FP32 planes: f_l, (phi u)_x, (phi u)_y, p, S; for FP16 storage also
-// phi_ref, T_ref and the FP32 rest populations g_0, h_0 (shifted), f_0
-int aux_planes(int storage) { return storage == LBM_STORE_FP32 ? 5 : 10; }
+using lbmk::aux_at;
+using lbmk::own0_at;
+using lbmk::pop_at;
+// own-site region, floats per site: (g_0, h_0, f_0, f_l), ((phi u)_x,
+// (phi u)_y, p, S), and for FP16 storage (phi_ref, T_ref)
+int aux_planes(int storage) { return storage == LBM_STORE_FP32 ? 8 : 10; }
 
 // D2Q9 directions and weights of the host-side state conversion (Eqs. 22-23)
 const int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -117,7 +120,7 @@ Layout make_layout(const lbm_params* p, int n, int storage) {
     for (int k = 0; k < n; ++k) {
         const uint64_t plane = (uint64_t)pitch_of(p[k].nx) * p[k].ny;
         for (int b = 0; b < 2; ++b) {
-            L.pop_off[b][k] = off; off = align_up(off + plane * 27 * elem_size(storage));
+            L.pop_off[b][k] = off; off = align_up(off + plane * lbmk::kPopElems * elem_size(storage));
             L.aux_off[b][k] = off; off = align_up(off + plane * aux_planes(storage) * sizeof(float));
         }
     }
@@ -521,23 +524,85 @@ int lbm_observables(lbm_handle* h, int32_t inst, double* out) {
 
 namespace {
 
+extern "C++" {
+// Planar host staging of one lattice's stored state, nx-compact: tp holds 27
+// planes of the storage type (set s, direction i in plane 9 s + i; for FP16
+// the rest planes 0, 9, 18 are unused), ta the FP32 carried planes in the
+// order of lbmk::aux_at (FP32: 5, f_l .. S; FP16: 10, adding phi_ref, T_ref
+// and the rest populations g_0, h_0, f_0). FP32 rest populations travel in
+// tp planes 0, 9, 18.
+template <typename T>
+int download_planar(lbm_handle* h, int32_t inst, std::vector<T>& tp, std::vector<float>& ta) {
+    const lbm_params& p = h->params[inst];
+    const Inst& I = h->inst[inst];
+    const int plane = (int)I.plane;
+    const bool half = h->storage == LBM_STORE_FP16;
+    std::vector<T> rp((size_t)lbmk::kPopElems * plane);
+    std::vector<float> ra((size_t)aux_planes(h->storage) * plane);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), I.pop[h->parity], rp.size() * sizeof(T),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ra.data(), I.aux[h->parity], ra.size() * sizeof(float),
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const size_t n = (size_t)p.nx * p.ny;
+    const int na = half ? 10 : 5;
+    tp.assign((size_t)27 * n, T());
+    ta.assign((size_t)na * n, 0.f);
+    for (int y = 0; y < p.ny; ++y)
+        for (int x = 0; x < p.nx; ++x) {
+            const size_t k = (size_t)y * p.nx + x;
+            const int site = y * I.pitch + x;
+            for (int set = 0; set < 3; ++set)
+                for (int i = 1; i < 9; ++i) tp[(9 * set + i) * n + k] = rp[pop_at(set, i, plane, site)];
+            for (int a = 0; a < na; ++a) ta[a * n + k] = ra[aux_at(a, plane, site)];
+            if (!half)
+                for (int set = 0; set < 3; ++set) tp[9 * set * n + k] = T(ra[own0_at(site, set)]);
+        }
+    return LBM_OK;
+}
+
+template <typename T>
+int upload_planar(lbm_handle* h, int32_t inst, const std::vector<T>& tp, const std::vector<float>& ta) {
+    const lbm_params& p = h->params[inst];
+    const Inst& I = h->inst[inst];
+    const int plane = (int)I.plane;
+    const bool half = h->storage == LBM_STORE_FP16;
+    std::vector<T> rp((size_t)lbmk::kPopElems * plane, T());
+    std::vector<float> ra((size_t)aux_planes(h->storage) * plane, 0.f);
+    const size_t n = (size_t)p.nx * p.ny;
+    const int na = half ? 10 : 5;
+    for (int y = 0; y < p.ny; ++y)
+        for (int x = 0; x < p.nx; ++x) {
+            const size_t k = (size_t)y * p.nx + x;
+            const int site = y * I.pitch + x;
+            for (int set = 0; set < 3; ++set)
+                for (int i = 1; i < 9; ++i) rp[pop_at(set, i, plane, site)] = tp[(9 * set + i) * n + k];
+            for (int a = 0; a < na; ++a) ra[aux_at(a, plane, site)] = ta[a * n + k];
+            if (!half)
+                for (int set = 0; set < 3; ++set) ra[own0_at(site, set)] = (float)tp[9 * set * n + k];
+        }
+    cudaError_t e = cudaMemcpyAsync(I.pop[h->parity], rp.data(), rp.size() * sizeof(T),
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(I.aux[h->parity], ra.data(), ra.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host arrays die on return
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e);
+}
+}  // extern "C++"
+
 // FP16 storage: download, then decode every population with the references of
 // the site it streams into (the same arithmetic as the kernels' decode).
 int get_state_fp16(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
-    std::vector<__half> tp((size_t)27 * n);
-    std::vector<float> ta((size_t)10 * n);
-    cudaError_t e = cudaMemcpy2DAsync(tp.data(), p.nx * sizeof(__half), I.pop[h->parity],
-                                      I.pitch * sizeof(__half), p.nx * sizeof(__half),
-                                      (size_t)27 * p.ny, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(ta.data(), p.nx * sizeof(float), I.aux[h->parity],
-                              I.pitch * sizeof(float), p.nx * sizeof(float), (size_t)10 * p.ny,
-                              cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
+    std::vector<__half> tp;
+    std::vector<float> ta;
+    const int rc = download_planar(h, inst, tp, ta);
+    if (rc != LBM_OK) return rc;
     const double L = h->init_L[inst];
     const float* phr = ta.data() + 5 * n;
     const float* Tr = ta.data() + 6 * n;
@@ -600,15 +665,8 @@ int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double
                 tp[(18 + i) * n + k] = __double2half((pops[(18 + i) * n + k] - fr) * 4096.0);
             }
         }
-    cudaError_t e = cudaMemcpy2DAsync(I.pop[h->parity], I.pitch * sizeof(__half), tp.data(),
-                                      p.nx * sizeof(__half), p.nx * sizeof(__half),
-                                      (size_t)27 * p.ny, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(I.aux[h->parity], I.pitch * sizeof(float), ta.data(),
-                              p.nx * sizeof(float), p.nx * sizeof(float), (size_t)10 * p.ny,
-                              cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
+    const int rc = upload_planar(h, inst, tp, ta);
+    if (rc != LBM_OK) return rc;
     h->initialised = true;
     h->have_obs = false;
     return LBM_OK;
@@ -623,16 +681,9 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
-    std::vector<float> tp((size_t)27 * n), ta((size_t)5 * n);
-    cudaError_t e = cudaMemcpy2DAsync(tp.data(), p.nx * sizeof(float), I.pop[h->parity],
-                                      I.pitch * sizeof(float), p.nx * sizeof(float),
-                                      (size_t)27 * p.ny, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(ta.data(), p.nx * sizeof(float), I.aux[h->parity],
-                              I.pitch * sizeof(float), p.nx * sizeof(float), (size_t)5 * p.ny,
-                              cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
+    std::vector<float> tp, ta;
+    const int rc = download_planar(h, inst, tp, ta);
+    if (rc != LBM_OK) return rc;
     const double L = h->init_L[inst];
     if (pops) {
         for (size_t k = 0; k < (size_t)27 * n; ++k) pops[k] = tp[k];
@@ -654,15 +705,8 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double*
     for (size_t k = 0; k < (size_t)27 * n; ++k) tp[k] = (float)pops[k];
     const double L = h->init_L[inst];
     for (size_t k = 0; k < n; ++k) tp[9 * n + k] = (float)(pops[9 * n + k] - L * (double)ta[k]);
-    cudaError_t e = cudaMemcpy2DAsync(I.pop[h->parity], I.pitch * sizeof(float), tp.data(),
-                                      p.nx * sizeof(float), p.nx * sizeof(float), (size_t)27 * p.ny,
-                                      cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(I.aux[h->parity], I.pitch * sizeof(float), ta.data(),
-                              p.nx * sizeof(float), p.nx * sizeof(float), (size_t)5 * p.ny,
-                              cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
+    const int rc = upload_planar(h, inst, tp, ta);
+    if (rc != LBM_OK) return rc;
     h->initialised = true;
     h->have_obs = false;
     return LBM_OK;

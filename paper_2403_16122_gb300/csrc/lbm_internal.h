@@ -22,16 +22,45 @@ enum : int {
     kStMask = 1 << 6,
 };
 
-// One lattice as the kernels see it. Populations of set s (0 g, 1 h, 2 f) and
-// direction i live in plane 9*s + i; a plane holds ny rows of `pitch`
-// elements. In FP32 storage the rest population h_0 is stored shifted by
-// -L f_l of the same site and step, which keeps every stored value O(1) (the
-// latent part of H is carried by the liquid-fraction plane instead).
+// Grouped state layout of one ping-pong buffer of a lattice. Sites are
+// numbered site = y * pitch + x, and plane = pitch * ny. Values that a site
+// pulls from the same neighbour, or keeps for itself, sit side by side, so
+// that one wide copy moves them:
+//   population region (elements of the storage type, FP32 or FP16):
+//     (g_i, h_i) of direction i = 1..8 at 2 (i - 1) plane + 2 site + set,
+//     f_i at (15 + i) plane + site                 -> 24 elements per site;
+//   own-site region (FP32):
+//     (g_0, h_0 - L f_l, f_0, f_l) at 4 site,
+//     ((phi u)_x, (phi u)_y, p, S) at 4 plane + 4 site,
+//     FP16 storage only: (phi_ref, T_ref) at 8 plane + 2 site.
+// h_0 is stored shifted by -L f_l of the same site and step, which keeps every
+// stored value O(1) (the latent part of H is carried by f_l instead).
+constexpr int kPopElems = 24;
+__host__ __device__ inline int gh_at(int i, int plane, int site, int set) {
+    return 2 * (i - 1) * plane + 2 * site + set;
+}
+__host__ __device__ inline int f_at(int i, int plane, int site) { return (15 + i) * plane + site; }
+__host__ __device__ inline int own0_at(int site, int c) { return 4 * site + c; }
+__host__ __device__ inline int own1_at(int plane, int site, int c) { return 4 * plane + 4 * site + c; }
+__host__ __device__ inline int ref_at(int plane, int site, int c) { return 8 * plane + 2 * site + c; }
+// Element offset of population (set, i) in the population region (i >= 1).
+__host__ __device__ inline int pop_at(int set, int i, int plane, int site) {
+    return set < 2 ? gh_at(i, plane, site, set) : f_at(i, plane, site);
+}
+// Carried field k of the own-site region: 0 f_l, 1 (phi u)_x, 2 (phi u)_y,
+// 3 p, 4 S, 5 phi_ref, 6 T_ref, 7/8/9 the rest populations g_0, h_0, f_0.
+__host__ __device__ inline int aux_at(int k, int plane, int site) {
+    return k == 0 ? own0_at(site, 3)
+                  : (k <= 4 ? own1_at(plane, site, k - 1)
+                            : (k <= 6 ? ref_at(plane, site, k - 5) : own0_at(site, k - 7)));
+}
+
+// One lattice as the kernels see it (state in the grouped layout above).
 struct Inst {
     int nx, ny, pitch, flags;
-    long long plane;          // elements per plane
-    void* pop[2];             // 27 planes, ping-pong buffers
-    float* aux[2];            // 5 planes: f_l, (phi u)_x, (phi u)_y, p, S
+    long long plane;          // sites per plane
+    void* pop[2];             // population regions, ping-pong buffers
+    float* aux[2];            // own-site regions
     int part_begin, part_end; // observable partials of this lattice's tiles
     // physics, single precision
     float L, Hs, Tm, Cp, Cpref, Tw;

@@ -100,7 +100,7 @@ __device__ __forceinline__ float ld_f16(const __half* p) {
 // (p (w_0 - 1) / c_s^2 for i = 0), and the deviation is scaled by 2^12; the
 // destination reads the source pressures from the carried p plane it loads
 // for the pressure gradient anyway. The rest populations g_0, h_0 (shifted)
-// and f_0 stay in FP32 (carried planes 7, 8, 9) and absorb the rounding
+// and f_0 stay in FP32 (own-site region) and absorb the rounding
 // errors of the site's eight 16-bit outgoing populations, so the zeroth
 // moment a site sends out (phi, H, and the f sum) is exact: rounding only
 // displaces a little of it along one link, which cancels between
@@ -110,14 +110,16 @@ struct Ref {
     float phi, T;
 };
 
+// Stored population (set, i) of site idx (grouped layout, see Inst); the rest
+// populations are FP32 in the own-site region for both storages.
 template <typename ST, bool NC>
-__device__ __forceinline__ float ldPop(const LatT<NC>& l, int plane, int idx) {
+__device__ __forceinline__ float ldPop(const LatT<NC>& l, int set, int i, int idx) {
+    if (i == 0) return ld_f32<NC>(l.Aaux + own0_at(idx, set));
     if constexpr (sizeof(ST) == 4) {
-        return ld_f32<NC>(l.A + (plane * l.plane + idx));
+        return ld_f32<NC>(l.A + pop_at(set, i, l.plane, idx));
     } else {
-        if (plane % 9 == 0) return ld_f32<NC>(l.Aaux + ((7 + plane / 9) * l.plane + idx));  // FP32 rest
         const __half* A = reinterpret_cast<const __half*>(l.A);
-        return ld_f16<NC>(A + (plane * l.plane + idx));
+        return ld_f16<NC>(A + pop_at(set, i, l.plane, idx));
     }
 }
 
@@ -140,7 +142,7 @@ __device__ __forceinline__ float f_rest(int i, float p) {
 }
 template <bool NC>
 __device__ __forceinline__ float ldAux(const LatT<NC>& l, int k, int idx) {
-    return ld_f32<NC>(l.Aaux + (k * l.plane + idx));
+    return ld_f32<NC>(l.Aaux + aux_at(k, l.plane, idx));
 }
 
 // Pull of set `set` (0 g, 1 h, 2 f) at lattice site (x, y): v[i] is the
@@ -154,7 +156,7 @@ __device__ __forceinline__ void pull_set(const LatT<NC>& l, int x, int y, float 
                                          float h0ref = 0.f, const float* pref = nullptr) {
     constexpr bool kFref = sizeof(ST) != 4 && SET == 2;  // f: source-pressure reference
     const int own = y * l.pitch + x;
-    v[0] = decode<ST, SET>(0, ldPop<ST>(l, 9 * SET, own), ref, Cpref, h0ref);
+    v[0] = decode<ST, SET>(0, ldPop<ST>(l, SET, 0, own), ref, Cpref, h0ref);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int xs = x - CX(i), ys = y - CY(i);
@@ -174,10 +176,10 @@ __device__ __forceinline__ void pull_set(const LatT<NC>& l, int x, int y, float 
             else { wall = true; dir |= (l.flags & kDirYhi) != 0; }
         }
         if (!wall) {
-            v[i] = decode<ST, SET>(i, ldPop<ST>(l, 9 * SET + i, ys * l.pitch + xs), ref, Cpref, h0ref);
+            v[i] = decode<ST, SET>(i, ldPop<ST>(l, SET, i, ys * l.pitch + xs), ref, Cpref, h0ref);
             if constexpr (kFref) v[i] += f_rest(i, pref[i]);
         } else {
-            float b = decode<ST, SET>(OPP(i), ldPop<ST>(l, 9 * SET + OPP(i), own), ref, Cpref, h0ref);
+            float b = decode<ST, SET>(OPP(i), ldPop<ST>(l, SET, OPP(i), own), ref, Cpref, h0ref);
             if constexpr (kFref) b += f_rest(OPP(i), pref[0]);  // bounced: the site itself
             if (SET == 1 && dir) b = -b + 2.0f * WGT(i) * abb;
             v[i] = b;
@@ -317,18 +319,23 @@ struct ArrPops {
     __device__ __forceinline__ float F(int i) const { return f[i]; }
 };
 struct SlotPops {
-    const float* s;  // this lane's column of the slot (planes 32 floats apart)
+    const float* s;  // the slot (layout: see the row staging below)
+    int lane;
     int hmask;       // bit i: h_i arrives through a Dirichlet wall
     float abb;       // Cp_ref T_w
-    __device__ __forceinline__ float rd(int q) const {
-        return *reinterpret_cast<const volatile float*>(s + q * 32);
+    __device__ __forceinline__ float rd(int off) const {
+        return *reinterpret_cast<const volatile float*>(s + off);
     }
-    __device__ __forceinline__ float G(int i) const { return rd(i); }
+    __device__ __forceinline__ float G(int i) const {
+        return rd(i == 0 ? 4 * lane : 256 + 64 * (i - 1) + 2 * lane);
+    }
     __device__ __forceinline__ float H(int i) const {
-        const float v = rd(9 + i);
+        const float v = rd(i == 0 ? 4 * lane + 1 : 256 + 64 * (i - 1) + 2 * lane + 1);
         return ((hmask >> i) & 1) ? -v + 2.0f * WGT(i) * abb : v;
     }
-    __device__ __forceinline__ float F(int i) const { return rd(18 + i); }
+    __device__ __forceinline__ float F(int i) const {
+        return rd(i == 0 ? 4 * lane + 2 : 768 + 32 * (i - 1) + lane);
+    }
 };
 
 // Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
@@ -401,7 +408,8 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     const float fsrc = 1.f - 0.5f * omega_f;
     const float TCp = T * P.Cp, TCpref = T * P.Cpref;
     const float uu15 = 1.5f * uu;
-    float g0n = 0.f, h0n = 0.f, f0n = 0.f, eg = 0.f, eh = 0.f, ef = 0.f;  // FP16 storage
+    float g0n = 0.f, h0n = 0.f, f0n = 0.f;  // rest populations
+    float eg = 0.f, eh = 0.f, ef = 0.f;     // FP16 storage: rounding carried to them
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float w = WGT(i);
@@ -427,15 +435,14 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         const float cF = CX(i) * Ftx + CY(i) * Fty;
         const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
         const float fn = fi - omega_f * (fi - feq) + fsrc * Fi;
-        if constexpr (sizeof(ST) == 4) {
+        if (i == 0) {
+            g0n = gn; h0n = hn; f0n = fn;  // own-site group, stored below
+        } else if constexpr (sizeof(ST) == 4) {
             float* B = static_cast<float*>(Bv);
-            B[i * plane + own] = gn;
-            B[(9 + i) * plane + own] = hn;
-            B[(18 + i) * plane + own] = fn;
+            *reinterpret_cast<float2*>(B + gh_at(i, plane, own, 0)) = make_float2(gn, hn);
+            B[f_at(i, plane, own)] = fn;
         } else {
-            if (i == 0) {
-                g0n = gn; h0n = hn; f0n = fn;
-            } else {
+            {
                 // deviations from the rest equilibria (g, h: destination's
                 // references dref[i]; f: this site's pressure), and what their
                 // rounding to 16 bits takes away from what the site sends
@@ -446,9 +453,8 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                 const __half qg = __float2half_rn(dg);
                 const __half qh = __float2half_rn(dh);
                 const __half qf = __float2half_rn(df);
-                B[i * plane + own] = qg;
-                B[(9 + i) * plane + own] = qh;
-                B[(18 + i) * plane + own] = qf;
+                *reinterpret_cast<__half2*>(B + gh_at(i, plane, own, 0)) = __halves2half2(qg, qh);
+                B[f_at(i, plane, own)] = qf;
                 eg += dg - __half2float(qg);
                 eh += dh - __half2float(qh);
                 ef += df - __half2float(qf);
@@ -456,19 +462,14 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         }
     }
     if constexpr (sizeof(ST) != 4) {  // the rest populations carry the rounding
-        Baux[7 * plane + own] = g0n + eg;
-        Baux[8 * plane + own] = h0n + eh;
-        Baux[9 * plane + own] = f0n + ef * kInvFScale;
+        g0n += eg;
+        h0n += eh;
+        f0n += ef * kInvFScale;
     }
-    Baux[own] = m.fl;
-    Baux[plane + own] = phiux;
-    Baux[2 * plane + own] = phiuy;
-    Baux[3 * plane + own] = pn;
-    Baux[4 * plane + own] = S;
-    if constexpr (sizeof(ST) != 4) {
-        Baux[5 * plane + own] = phi;  // references of this site for the next step
-        Baux[6 * plane + own] = T;
-    }
+    *reinterpret_cast<float4*>(Baux + own0_at(own, 0)) = make_float4(g0n, h0n, f0n, m.fl);
+    *reinterpret_cast<float4*>(Baux + own1_at(plane, own, 0)) = make_float4(phiux, phiuy, pn, S);
+    if constexpr (sizeof(ST) != 4)  // references of this site for the next step
+        *reinterpret_cast<float2*>(Baux + ref_at(plane, own, 0)) = make_float2(phi, T);
 
     if (OBS) {
         const double dphi = phi, dfs = fs;
@@ -735,7 +736,7 @@ __device__ __forceinline__ void pull_rows(const LatT<NC>& l, int xc, int xm, int
     for (int i = 0; i < 9; ++i) {
         const int r = CY(i) > 0 ? rm : (CY(i) < 0 ? rp : r0);   // source row y - cy
         const int c = CX(i) > 0 ? xm : (CX(i) < 0 ? xp : xc);   // source column x - cx
-        v[i] = decode<ST, SET>(i, ldPop<ST>(l, 9 * SET + i, r + c), ref, Cpref, h0ref);
+        v[i] = decode<ST, SET>(i, ldPop<ST>(l, SET, i, r + c), ref, Cpref, h0ref);
         if constexpr (sizeof(ST) != 4 && SET == 2) {
             if (i) v[i] += f_rest(i, pref[i]);
         }
@@ -786,17 +787,23 @@ __device__ __forceinline__ float strip_wet_ghost(float a, float b, float outer_a
 
 // ---------------------------------------------------------------------------
 // Row staging: each lane copies, asynchronously and several rows ahead, every
-// value it will consume from a lattice row into its own column of a per-warp
-// ring of shared-memory slots: the 27 populations pulled into its site (for a
-// link that crosses a wall, the site's own opposite population, i.e. the
-// bounce-back source) and the carried fields of its site. A lane reads back
+// value it will consume from a lattice row into its own part of a per-warp
+// ring of shared-memory slots: the populations pulled into its site (for a
+// link that crosses a wall, the site's own opposite populations, i.e. the
+// bounce-back sources) and the own-site group of its site. A lane reads back
 // only what it copied itself, so no warp or block barrier is involved;
-// cp.async.wait_group orders the copies before the reads.
-// Slot planes (32 lanes of 4 bytes each): 0..26 the pulled populations, 27 f_l,
-// 28 (phi u)_x, 29 (phi u)_y, 30 p, 31 S; FP16 storage adds 32 phi_ref and
-// 33 T_ref, and its planes 0, 9 and 18 hold the FP32 rest populations, the
-// others the aligned 32-bit word that contains the wanted 16-bit value.
+// cp.async.wait_group orders the copies before the reads. With the grouped
+// layout one copy moves a (g_i, h_i) pair (8 bytes, FP16: 4) and one four
+// own-site values (16 bytes), so a row takes 18 copies instead of 32.
+// Slot layout in floats, lane l: 4l + c the own-site group (g_0, h_0, f_0,
+// f_l), 128 + 4l + c ((phi u)_x, (phi u)_y, p, S), 256 + 64 (i - 1) + 2l + s
+// the pair (g_i, h_i), 768 + 32 (i - 1) + l f_i, and for FP16 storage
+// 1024 + 2l + c (phi_ref, T_ref). FP16 pairs and f_i arrive as the aligned
+// 32-bit word that holds them; decoded values are written back in place.
 // ---------------------------------------------------------------------------
+constexpr int kSlotO1 = 128, kSlotGH = 256, kSlotF = 768, kSlotR = 1024;
+__device__ __forceinline__ int slot_gh(int i, int lane) { return kSlotGH + 64 * (i - 1) + 2 * lane; }
+__device__ __forceinline__ int slot_f(int i, int lane) { return kSlotF + 32 * (i - 1) + lane; }
 template <typename ST>
 __host__ __device__ constexpr int stage_planes() { return sizeof(ST) == 4 ? 32 : 34; }
 template <typename ST>
@@ -805,6 +812,14 @@ __host__ __device__ constexpr int slot_floats() { return stage_planes<ST>() * 32
 __device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(float* dst_smem, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst_smem, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -815,50 +830,41 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Issue the copies of lattice row r (possibly -1 or ny for periodic y) into
-// `slot` (this lane's column of one ring slot). macro_only: only what the
-// local macroscopic step needs (g, h, f_l, p, S and the references).
+// this lane's part of the ring slot at `slot`. macro_only: only what the
+// local macroscopic step needs (everything but f_i).
 template <typename ST, bool NC>
-__device__ __forceinline__ void stage_row(const LatT<NC>& l, int xc, int xm, int xp, bool py, int r,
-                                          bool macro_only, float* slot) {
+__device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, int xm, int xp,
+                                          bool py, int r, bool macro_only, float* slot) {
     constexpr bool kHalf = sizeof(ST) != 4;
-    const int ny = l.ny;
+    const int ny = l.ny, plane = l.plane;
     const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
     const int rr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
     const int ym = rr == 0 ? ny - 1 : rr - 1, yp = rr == ny - 1 ? 0 : rr + 1;
     const int o0 = rr * l.pitch, om = ym * l.pitch, op = yp * l.pitch;
     const int own = o0 + xc;
+    cp_async16(slot + 4 * lane, l.Aaux + own0_at(own, 0));
+    cp_async16(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(plane, own, 0));
+    if constexpr (kHalf) cp_async8(slot + kSlotR + 2 * lane, l.Aaux + ref_at(plane, own, 0));
+    const __half* A16 = reinterpret_cast<const __half*>(l.A);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        const int set = q / 9, i = q % 9;
-        if (macro_only && set == 2) continue;
-        if (kHalf && i == 0) {  // FP32 rest population (carried planes 7, 8, 9)
-            cp_async4(slot + q * 32, l.Aaux + (7 + set) * l.plane + own);
-            continue;
-        }
+    for (int i = 1; i < 9; ++i) {
         const int cy = CY(i), cx = CX(i);
         const bool wall = (cy > 0 && wlo) || (cy < 0 && whi);
-        const int src = wall ? (9 * set + OPP(i)) * l.plane + own
-                             : q * l.plane + (cy > 0 ? om : (cy < 0 ? op : o0)) +
-                                   (cx > 0 ? xm : (cx < 0 ? xp : xc));
+        const int si = wall ? OPP(i) : i;
+        const int site = wall ? own : (cy > 0 ? om : (cy < 0 ? op : o0)) +
+                                          (cx > 0 ? xm : (cx < 0 ? xp : xc));
         if constexpr (kHalf) {
-            // planes and rows hold an even number of 16-bit values, so the
-            // aligned word lies inside the row
-            const __half* A16 = reinterpret_cast<const __half*>(l.A);
-            cp_async4(slot + q * 32, reinterpret_cast<const float*>(A16 + (src & ~1)));
+            // planes and rows hold an even number of 16-bit values, so every
+            // aligned word lies inside its row
+            cp_async4(slot + slot_gh(i, lane),
+                      reinterpret_cast<const float*>(A16 + gh_at(si, plane, site, 0)));
+            if (!macro_only)
+                cp_async4(slot + slot_f(i, lane),
+                          reinterpret_cast<const float*>(A16 + (f_at(si, plane, site) & ~1)));
         } else {
-            cp_async4(slot + q * 32, l.A + src);
+            cp_async8(slot + slot_gh(i, lane), l.A + gh_at(si, plane, site, 0));
+            if (!macro_only) cp_async4(slot + slot_f(i, lane), l.A + f_at(si, plane, site));
         }
-    }
-    cp_async4(slot + 27 * 32, l.Aaux + own);
-    if (!macro_only) {
-        cp_async4(slot + 28 * 32, l.Aaux + l.plane + own);
-        cp_async4(slot + 29 * 32, l.Aaux + 2 * l.plane + own);
-    }
-    cp_async4(slot + 30 * 32, l.Aaux + 3 * l.plane + own);
-    cp_async4(slot + 31 * 32, l.Aaux + 4 * l.plane + own);
-    if constexpr (kHalf) {
-        cp_async4(slot + 32 * 32, l.Aaux + 5 * l.plane + own);
-        cp_async4(slot + 33 * 32, l.Aaux + 6 * l.plane + own);
     }
 }
 
@@ -875,39 +881,42 @@ __device__ __forceinline__ unsigned half_sel(int col) { return (col & 1) ? 0x323
 // site's own pressure pref[0] on bounced links); for h at a Dirichlet wall
 // row the bounced populations become anti-bounce-back, -h + 2 w_i Cp_ref T_w.
 template <int SET, typename ST = float>
-__device__ __forceinline__ void staged_set(const float* slot, int r, int ny, bool py, int flags,
-                                           float abb, float v[9], const ColPar& par = ColPar{0, 0, 0},
+__device__ __forceinline__ void staged_set(const float* slot, int lane, int r, int ny, bool py,
+                                           int flags, float abb, float v[9],
+                                           const ColPar& par = ColPar{0, 0, 0},
                                            const Ref& ref = Ref{0.f, 0.f}, float Cpref = 0.f,
                                            const float* pref = nullptr) {
     const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
+    v[0] = slot[4 * lane + SET];  // FP32 rest population (h_0 shifted)
     if constexpr (sizeof(ST) == 4) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = slot[(9 * SET + i) * 32];
+        for (int i = 1; i < 9; ++i) v[i] = SET < 2 ? slot[slot_gh(i, lane) + SET] : slot[slot_f(i, lane)];
         if (SET == 1 && !py) {
             const bool lo = wlo && (flags & kDirYlo), hi = whi && (flags & kDirYhi);
 #pragma unroll
             for (int i = 1; i < 9; ++i)
                 if ((CY(i) > 0 && lo) || (CY(i) < 0 && hi)) v[i] = -v[i] + 2.0f * WGT(i) * abb;
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 1; i < 9; ++i) {
         const bool wall = (CY(i) > 0 && wlo) || (CY(i) < 0 && whi);
-        if (i == 0) {
-            v[i] = slot[(9 * SET) * 32];
+        if (SET < 2) {
+            const unsigned w = __float_as_uint(slot[slot_gh(i, lane)]);
+            const float raw =
+                __half2float(__ushort_as_half((unsigned short)(SET == 0 ? (w & 0xffffu) : (w >> 16))));
+            v[i] = SET == 0 ? raw + WGT(i) * ref.phi : raw + WGT(i) * Cpref * ref.T;
         } else {
-            const unsigned w = __float_as_uint(slot[(9 * SET + i) * 32]);
+            const unsigned w = __float_as_uint(slot[slot_f(i, lane)]);
             const unsigned sel = wall ? par.c : (CX(i) > 0 ? par.m : (CX(i) < 0 ? par.p : par.c));
             const float raw = __half2float(__ushort_as_half((unsigned short)__byte_perm(w, 0u, sel)));
-            if (SET == 0) v[i] = raw + WGT(i) * ref.phi;
-            if (SET == 1) v[i] = raw + WGT(i) * Cpref * ref.T;
-            if (SET == 2) v[i] = raw * kInvFScale + f_rest(i, wall ? pref[0] : pref[i]);
+            v[i] = raw * kInvFScale + f_rest(i, wall ? pref[0] : pref[i]);
         }
         if (SET == 1 && wall) {
             const bool dir = (wlo && (flags & kDirYlo)) || (whi && (flags & kDirYhi));
             if (dir) v[i] = -v[i] + 2.0f * WGT(i) * abb;
         }
+    }
     }
 }
 
@@ -988,35 +997,38 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     const int y0 = W.y0;
     const int R = W.y1 - y0 + 2;
     const bool has_lo = y0 >= 1 || c.py, has_hi = W.y1 < ny || c.py;
-    float* const my_ring = ring + lane;
-    auto slot = [&](int j) { return my_ring + (j % (STG > 0 ? STG : 1)) * slot_floats<ST>(); };
+    auto slot = [&](int j) { return ring + (j % (STG > 0 ? STG : 1)) * slot_floats<ST>(); };
     auto issue = [&](int j) {
         if constexpr (STG > 0) {
             if (j < R && (j > 0 || has_lo) && (j < R - 1 || has_hi))
-                stage_row<ST>(l, c.xc, c.xm, c.xp, c.py, y0 - 1 + j, j == 0 || j == R - 1, slot(j));
+                stage_row<ST>(l, lane, c.xc, c.xm, c.xp, c.py, y0 - 1 + j, j == 0 || j == R - 1,
+                              slot(j));
             cp_async_commit();  // possibly empty: one group per ring index
         }
     };
     const ColPar par{half_sel(c.xc), half_sel(c.xm), half_sel(c.xp)};
     auto slot_ref = [&](const float* sl) {
         Ref r{0.f, 0.f};
-        if constexpr (kHalf) { r.phi = sl[32 * 32]; r.T = sl[33 * 32]; }
+        if constexpr (kHalf) { r.phi = sl[kSlotR + 2 * lane]; r.T = sl[kSlotR + 2 * lane + 1]; }
         return r;
     };
     auto row_macro_staged = [&](int j, int y, Macro& m, float& p, float& S, Ref& r) {
         float gg[9], hh[9];
         const float* sl = slot(j);
         r = slot_ref(sl);
-        staged_set<0, ST>(sl, y, ny, c.py, l.flags, abb, gg, par, r, P.Cpref);
-        staged_set<1, ST>(sl, y, ny, c.py, l.flags, abb, hh, par, r, P.Cpref);
+        staged_set<0, ST>(sl, lane, y, ny, c.py, l.flags, abb, gg, par, r, P.Cpref);
+        staged_set<1, ST>(sl, lane, y, ny, c.py, l.flags, abb, hh, par, r, P.Cpref);
         if constexpr (kHalf) {  // keep the decoded values for the collision
             float* ws = const_cast<float*>(sl);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) { ws[i * 32] = gg[i]; ws[(9 + i) * 32] = hh[i]; }
+            for (int i = 1; i < 9; ++i) {
+                ws[slot_gh(i, lane)] = gg[i];
+                ws[slot_gh(i, lane) + 1] = hh[i];
+            }
         }
-        m = local_macro(P, gg, hh, sl[27 * 32]);
-        p = sl[30 * 32];
-        S = sl[31 * 32];
+        m = local_macro(P, gg, hh, sl[4 * lane + 3]);
+        p = sl[kSlotO1 + 4 * lane + 2];
+        S = sl[kSlotO1 + 4 * lane + 3];
         note_outer(y);
     };
 
@@ -1076,7 +1088,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                 }
             }
             if constexpr (STG > 0)
-                staged_set<2, ST>(slot(jy), y, ny, c.py, l.flags, abb, f, par, rO, P.Cpref, pref);
+                staged_set<2, ST>(slot(jy), lane, y, ny, c.py, l.flags, abb, f, par, rO, P.Cpref,
+                                  pref);
             else
                 pull_row<2, ST>(l, c, y, abb, f, rO, P.Cpref, P.h0ref, pref);
         };
@@ -1084,8 +1097,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         if constexpr (STG > 0) {
             const float* sl = slot(jy);
             if constexpr (!kHalf && !kSlotPops) pull_f();
-            phiux_p = sl[28 * 32];
-            phiuy_p = sl[29 * 32];
+            phiux_p = sl[kSlotO1 + 4 * lane];
+            phiuy_p = sl[kSlotO1 + 4 * lane + 1];
         } else {
             if constexpr (!kHalf) pull_f();
             phiux_p = ldAux(l, 1, own);
@@ -1114,7 +1127,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             if constexpr (STG > 0) {  // decoded f for the collision's slot reads
                 float* ws = slot(jy);
 #pragma unroll
-                for (int i = 1; i < 9; ++i) ws[(18 + i) * 32] = f[i];
+                for (int i = 1; i < 9; ++i) ws[slot_f(i, lane)] = f[i];
             }
         }
 
@@ -1163,7 +1176,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                     for (int i = 1; i < 9; ++i)
                         if ((CY(i) > 0 && lo) || (CY(i) < 0 && hi)) hmask |= 1 << i;
                 }
-                site_update<OBS, ST>(P, l.flags, mO, SlotPops{slot(jy), hmask, abb}, phiux_p,
+                site_update<OBS, ST>(P, l.flags, mO, SlotPops{slot(jy), lane, hmask, abb}, phiux_p,
                                      phiuy_p, st, B, Baux, l.plane, own, c.xc == nx / 2,
                                      y == ny / 2, ob, dref);
             }
@@ -1171,8 +1184,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             // g and h of row y were pulled one row earlier: these loads hit L1
             float g[9], h[9];
             if constexpr (STG > 0) {
-                staged_set<0, ST>(slot(jy), y, ny, c.py, l.flags, abb, g, par, rO, P.Cpref);
-                staged_set<1, ST>(slot(jy), y, ny, c.py, l.flags, abb, h, par, rO, P.Cpref);
+                staged_set<0, ST>(slot(jy), lane, y, ny, c.py, l.flags, abb, g, par, rO, P.Cpref);
+                staged_set<1, ST>(slot(jy), lane, y, ny, c.py, l.flags, abb, h, par, rO, P.Cpref);
             } else {
                 pull_row<0, ST>(l, c, y, abb, g, rO, P.Cpref, P.h0ref);
                 pull_row<1, ST>(l, c, y, abb, h, rO, P.Cpref, P.h0ref);
@@ -1219,7 +1232,7 @@ template <int WARPS, int MINB, int STG, bool OBS, typename ST>
 __global__ void __launch_bounds__(WARPS * 32, MINB)
 step_strip_staged(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
                   int parity, double* __restrict__ partials) {
-    extern __shared__ float ring_smem[];
+    extern __shared__ __align__(16) float ring_smem[];
     // Programmatic dependent launch: let the next step's grid be scheduled as
     // soon as every CTA of this one has started, and touch no lattice data
     // before the previous step's grid has completed (a no-op when launched
@@ -1287,7 +1300,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB)
 step_strip_persistent(const Inst* __restrict__ insts, const Item* __restrict__ items,
                       int n_items, int parity0, int nsteps, unsigned* bar, int* err,
                       unsigned long long limit_ns) {
-    extern __shared__ float ring_smem[];
+    extern __shared__ __align__(16) float ring_smem[];
     float* ring = ring_smem + (threadIdx.x >> 5) * (STG * slot_floats<ST>());
     const int warp = blockIdx.x * WARPS + (threadIdx.x >> 5);
     const int stride = gridDim.x * WARPS;
@@ -1326,20 +1339,25 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
         const double T = c.Tm + (H - c.Hs - c.L * fl) / c.Cp;  // Eq. 9b
         float* P = static_cast<float*>(I.pop[parity]);
         float* A = I.aux[parity];
+        const int plane = (int)I.plane, site = (int)idx;
         for (int i = 0; i < 9; ++i) {
             const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-            P[(long long)i * I.plane + idx] = (float)(w * ph);                     // Eq. 24, u = 0
+            const float g = (float)(w * ph);                                       // Eq. 24, u = 0
             double hq = (i == 0) ? H - c.Cpref * T + w * c.Cp * T * (c.Cpref / c.Cp)
                                  : w * c.Cp * T * (c.Cpref / c.Cp);                // Eq. 28, u = 0
             if (i == 0) hq -= c.L * fl;                                            // shifted h_0
-            P[(long long)(9 + i) * I.plane + idx] = (float)hq;
-            P[(long long)(18 + i) * I.plane + idx] = 0.0f;  // Eq. 31 vanishes at p = 0, u = 0
+            if (i == 0) {  // Eq. 31 vanishes at p = 0, u = 0
+                A[own0_at(site, 0)] = g;
+                A[own0_at(site, 1)] = (float)hq;
+                A[own0_at(site, 2)] = 0.f;
+            } else {
+                P[gh_at(i, plane, site, 0)] = g;
+                P[gh_at(i, plane, site, 1)] = (float)hq;
+                P[f_at(i, plane, site)] = 0.f;
+            }
         }
-        A[idx] = (float)fl;
-        A[I.plane + idx] = 0.f;
-        A[2 * I.plane + idx] = 0.f;
-        A[3 * I.plane + idx] = 0.f;
-        A[4 * I.plane + idx] = 0.f;
+        A[own0_at(site, 3)] = (float)fl;
+        for (int k = 0; k < 4; ++k) A[own1_at(plane, site, k)] = 0.f;
     }
 }
 
@@ -1385,24 +1403,21 @@ __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
             const float phd = (float)phi0[kd];
             const float Td = (float)init_T(c, T0[kd]);
             if (i == 0) {  // rest populations in FP32
-                A[7 * plane + idx] = (float)(w * ph);                                 // Eq. 24
-                A[8 * plane + idx] =
+                A[own0_at(idx, 0)] = (float)(w * ph);                                 // Eq. 24
+                A[own0_at(idx, 1)] =
                     (float)(H - c.Cpref * T + w * c.Cp * T * (c.Cpref / c.Cp) - c.L * fl);  // shifted h_0
-                A[9 * plane + idx] = 0.f;
+                A[own0_at(idx, 2)] = 0.f;
                 continue;
             }
-            P[i * plane + idx] = __double2half(w * ph - (double)(wf * phd));      // Eq. 24, u = 0
-            P[(9 + i) * plane + idx] =
+            P[gh_at(i, plane, idx, 0)] = __double2half(w * ph - (double)(wf * phd));  // Eq. 24, u = 0
+            P[gh_at(i, plane, idx, 1)] =
                 __double2half(w * c.Cp * T * (c.Cpref / c.Cp) - (double)(wf * I.Cpref * Td));  // Eq. 28
-            P[(18 + i) * plane + idx] = __float2half_rn(0.f);  // Eq. 31 vanishes at p = 0, u = 0
+            P[f_at(i, plane, idx)] = __float2half_rn(0.f);  // Eq. 31 vanishes at p = 0, u = 0
         }
-        A[idx] = (float)fl;
-        A[plane + idx] = 0.f;
-        A[2 * plane + idx] = 0.f;
-        A[3 * plane + idx] = 0.f;
-        A[4 * plane + idx] = 0.f;
-        A[5 * plane + idx] = phr;
-        A[6 * plane + idx] = Tr;
+        A[own0_at(idx, 3)] = (float)fl;
+        for (int k = 0; k < 4; ++k) A[own1_at(plane, idx, k)] = 0.f;
+        A[ref_at(plane, idx, 0)] = phr;
+        A[ref_at(plane, idx, 1)] = Tr;
     }
 }
 

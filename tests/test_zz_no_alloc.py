@@ -30,22 +30,47 @@ def env():
 
 
 def _to_device(torch, pops, aux, L, pitch):
-    """Host state (h_0 unshifted, doubles) -> device buffers in the library's
-    layout: FP32 planes of `pitch` floats per row, h_0 stored as h_0 - L f_l."""
+    """Host state (27 population planes with h_0 unshifted, 5 carried planes;
+    doubles) -> device buffers in the library's grouped FP32 layout: the
+    population buffer as 8 planes of (g_i, h_i) pairs then 8 planes of f_i,
+    the own-site buffer as (g_0, h_0 - L f_l, f_0, f_l) then
+    ((phi u)_x, (phi u)_y, p, S) per site; rows of `pitch` sites."""
     ny, nx = pops.shape[1:]
-    P = torch.zeros((27, ny, pitch), dtype=torch.float32, device="cuda")
-    A = torch.zeros((5, ny, pitch), dtype=torch.float32, device="cuda")
-    pp = pops.copy()
-    pp[9] = pops[9] - L * aux[0]
-    P[:, :, :nx] = torch.from_numpy(pp.astype(np.float32)).cuda()
-    A[:, :, :nx] = torch.from_numpy(aux.astype(np.float32)).cuda()
-    return P, A
+    P = np.zeros((24, ny, pitch), np.float32)
+    A = np.zeros((8, ny, pitch), np.float32)
+    P4 = P[:16].reshape(8, ny, pitch, 2)  # pair planes viewed as (i, y, x, g/h)
+    for i in range(1, 9):
+        P4[i - 1, :, :nx, 0] = pops[i]
+        P4[i - 1, :, :nx, 1] = pops[9 + i]
+        P[15 + i, :, :nx] = pops[18 + i]
+    O = A.reshape(2, ny, pitch, 4)
+    O[0, :, :nx, 0] = pops[0]
+    O[0, :, :nx, 1] = pops[9] - L * aux[0]
+    O[0, :, :nx, 2] = pops[18]
+    O[0, :, :nx, 3] = aux[0]
+    for k in range(4):
+        O[1, :, :nx, k] = aux[1 + k]
+    return torch.from_numpy(P).cuda(), torch.from_numpy(A).cuda()
 
 
 def _to_host(P, A, L, nx):
-    pops = P[:, :, :nx].double().cpu().numpy()
-    aux = A[:, :, :nx].double().cpu().numpy()
-    pops[9] = pops[9] + L * aux[0]
+    P = P.cpu().numpy().astype(np.float64)
+    A = A.cpu().numpy().astype(np.float64)
+    _, ny, pitch = P.shape
+    P4 = P[:16].reshape(8, ny, pitch, 2)
+    O = A.reshape(2, ny, pitch, 4)
+    pops = np.zeros((27, ny, nx))
+    aux = np.zeros((5, ny, nx))
+    for i in range(1, 9):
+        pops[i] = P4[i - 1, :, :nx, 0]
+        pops[9 + i] = P4[i - 1, :, :nx, 1]
+        pops[18 + i] = P[15 + i, :, :nx]
+    aux[0] = O[0, :, :nx, 3]
+    pops[0] = O[0, :, :nx, 0]
+    pops[9] = O[0, :, :nx, 1] + L * aux[0]
+    pops[18] = O[0, :, :nx, 2]
+    for k in range(4):
+        aux[1 + k] = O[1, :, :nx, k]
     return pops, aux
 
 
@@ -60,8 +85,8 @@ def test_noalloc_step_matches_handle_step_twice(env):
     pops, aux = lat.get_state()
 
     bufs = [_to_device(torch, pops, aux, L, pitch),
-            (torch.zeros((27, p["ny"], pitch), dtype=torch.float32, device="cuda"),
-             torch.zeros((5, p["ny"], pitch), dtype=torch.float32, device="cuda"))]
+            (torch.zeros((24, p["ny"], pitch), dtype=torch.float32, device="cuda"),
+             torch.zeros((8, p["ny"], pitch), dtype=torch.float32, device="cuda"))]
     d_obs = torch.zeros(lbm.LBM_OBS_COUNT, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
