@@ -338,6 +338,27 @@ struct SlotPops {
     }
 };
 
+// Per-thread observable sums of the sites it updates. The sums run in FP32
+// with Neumaier's compensation (the running sum and the rounding error each
+// addition dropped), and (s + c) is taken in FP64 before the warp, block and
+// item reductions, which are FP64: the result matches an FP64 running sum of
+// the same FP32 per-site values to well below their own rounding, without
+// FP64 arithmetic per site (the FP64 rate of the GPU is a small fraction of
+// its FP32 rate). Slot 9 is a maximum, not a sum.
+struct ObsAcc {
+    float s[kObs], c[kObs];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) { s[j] = 0.f; c[j] = 0.f; }
+    }
+    __device__ __forceinline__ void add(int j, float x) {
+        const float t = s[j] + x;
+        c[j] += fabsf(s[j]) >= fabsf(x) ? (s[j] - t) + x : (x - t) + s[j];
+        s[j] = t;
+    }
+    __device__ __forceinline__ double total(int j) const { return (double)s[j] + (double)c[j]; }
+};
+
 // Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
 // three collisions (Eqs. 21, 25, 27-28, 30-33) and the store of the
 // post-collision populations and carried fields of one site. The order of
@@ -349,7 +370,7 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                                             float phiux_p, float phiuy_p, const Stencil& st,
                                             void* __restrict__ Bv, float* __restrict__ Baux,
                                             int plane, int own, bool on_col, bool on_row,
-                                            double ob[kObs], const Ref* dref = nullptr) {
+                                            ObsAcc& ob, const Ref* dref = nullptr) {
     const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
     const float gphx = st.gphx, gphy = st.gphy, lph = st.lph, grx = st.grx, gry = st.gry;
     const float gpx = st.gpx, gpy = st.gpy, gSx = st.gSx, gSy = st.gSy;
@@ -472,20 +493,23 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         *reinterpret_cast<float2*>(Baux + ref_at(plane, own, 0)) = make_float2(phi, T);
 
     if (OBS) {
-        const double dphi = phi, dfs = fs;
-        ob[0] += dphi;
-        ob[1] += dfs;
-        ob[2] += (double)m.Hp + (double)P.L * (double)m.flp;
-        ob[3] += rho;
-        ob[4] += dfs * P.rho_s + (1.0 - dfs) * (double)clamp01(phi) * P.rho_l;
-        ob[5] += mdot;
-        ob[6] += dphi * (double)mdot;
-        ob[7] += on_col ? dfs : 0.0;
-        ob[8] += on_row ? dfs : 0.0;
-        ob[9] = fmax(ob[9], sqrt((double)uu));
+        ob.add(0, phi);
+        ob.add(1, fs);
+        // H = H' + L f_l^{n-1}: the product enters with its exact rounding error
+        const float lf = P.L * m.flp;
+        ob.add(2, m.Hp);
+        ob.add(2, lf);
+        ob.add(2, fmaf(P.L, m.flp, -lf));
+        ob.add(3, rho);
+        ob.add(4, fs * P.rho_s + (1.f - fs) * clamp01(phi) * P.rho_l);
+        ob.add(5, mdot);
+        ob.add(6, phi * mdot);
+        if (on_col) ob.add(7, fs);
+        if (on_row) ob.add(8, fs);
+        ob.s[9] = fmaxf(ob.s[9], sqrtf(uu));
         const bool bad = !isfinite(phi) || !isfinite(m.Hp) || !isfinite(ux) || !isfinite(uy) ||
                          !isfinite(pn);
-        ob[10] += bad ? 1.0 : 0.0;
+        if (bad) ob.add(10, 1.f);
     }
 }
 
@@ -654,11 +678,8 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
     __syncthreads();
 
     // ---- phase D: stencils, forces, collisions, store ----
-    double ob[kObs];
-    if (OBS) {
-#pragma unroll
-        for (int j = 0; j < kObs; ++j) ob[j] = 0.0;
-    }
+    ObsAcc ob;
+    if (OBS) ob.zero();
     if (active) {
         Stencil st;
         {
@@ -687,7 +708,12 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
         site_update<OBS>(P, l.flags, m, ArrPops{g, h, f}, phiux_p, phiuy_p, st, B, Baux, l.plane,
                          y * l.pitch + x, x == l.nx / 2, y == l.ny / 2, ob);
     }
-    if (OBS) block_reduce_obs<NT>(ob, partials + (long long)T.part * kObs);
+    if (OBS) {
+        double v[kObs];
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) v[j] = ob.total(j);
+        block_reduce_obs<NT>(v, partials + (long long)T.part * kObs);
+    }
 }
 
 template <int TX, int TY, bool OBS>
@@ -1032,11 +1058,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         note_outer(y);
     };
 
-    double ob[kObs];
-    if (OBS) {
-#pragma unroll
-        for (int j = 0; j < kObs; ++j) ob[j] = 0.0;
-    }
+    ObsAcc ob;
+    if (OBS) ob.zero();
 
     // rows y-1 (m), y (0) and y+1 (p) of phi, rho, p^{n-1}, S^{n-1} (and T)
     float phm = 0.f, ph0, php = 0.f, rhm = 0.f, rh0, rhp = 0.f;
@@ -1206,7 +1229,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     if (OBS) {
 #pragma unroll
         for (int j = 0; j < kObs; ++j) {
-            double v = ob[j];
+            double v = ob.total(j);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double u = __shfl_xor_sync(0xffffffffu, v, o);
