@@ -98,6 +98,12 @@ typedef struct lbm_params {
                             switches on (solid forms only in liquid), > 0     */
     double normal_eps;   /* interface-normal regularisation, > 0:
                             n = grad phi / sqrt(|grad phi|^2 + eps^2)         */
+    double gx, gy;       /* gravity of the Boussinesq force (Section 4.3)     */
+    double beta_T;       /* volumetric expansion coefficient; with gx, gy it
+                            adds F_g = -rho_0 g beta_T (T - T_ref) to the
+                            force of every site (0 switches it off)          */
+    double T_ref;        /* reference temperature of F_g                      */
+    double rho_0;        /* reference density of F_g                          */
 } lbm_params;
 
 /* Observables of the most recent step of an instance (index into the

@@ -473,7 +473,11 @@ static void step_once(oracle_state* s) {
             double muphi = 4.0 * s->beta * (ph - 1.0) * ph * (ph - 0.5) - s->kappa * lph;
             double Fx = muphi * gphx, Fy = muphi * gphy;
             if (p->st_mask_liquid) { Fx *= (1.0 - fs); Fy *= (1.0 - fs); }
-            /* F = F_s + G with G = 0 (no body force in this scheme's inputs). */
+            /* F = F_s + F_g with the Boussinesq buoyancy of Section 4.3,
+               F_g = -rho_0 g beta (T - T_ref), at every site (R22); zero
+               unless gravity and beta are given. */
+            Fx += -p->rho_0 * p->beta_T * (T - p->T_ref) * p->gx;
+            Fy += -p->rho_0 * p->beta_T * (T - p->T_ref) * p->gy;
 
             const double* fpre = s->pre + (int64_t)(SET_F * 9) * n;
             double mx = 0.0, my = 0.0, fsum_ne0 = 0.0;

@@ -55,6 +55,10 @@ typedef struct oracle_params {
                               switches on (solid forms only in the liquid)        */
     double normal_eps;     /* regularisation of the interface normal:
                               n = grad phi / sqrt(|grad phi|^2 + eps^2)           */
+    double gx, gy;         /* gravity vector of the Boussinesq force (Section 4.3) */
+    double beta_T;         /* volumetric expansion coefficient beta               */
+    double T_ref;          /* reference temperature of the Boussinesq force       */
+    double rho_0;          /* reference density rho_0 of the Boussinesq force     */
 } oracle_params;
 
 /* Observables of the most recent step (indices into the output array). */

@@ -49,6 +49,9 @@ bool valid_params(const lbm_params& p) {
     if (!(p.pc_ramp > 0)) return false;
     if (!(p.normal_eps > 0) || !isfinite(p.normal_eps)) return false;
     if (!isfinite(p.T_m) || !isfinite(p.T_w) || !isfinite(p.sigma)) return false;
+    if (!isfinite(p.gx) || !isfinite(p.gy) || !isfinite(p.beta_T) || !isfinite(p.T_ref) ||
+        !isfinite(p.rho_0))
+        return false;
     return true;
 }
 
@@ -893,6 +896,10 @@ void inst_from_params(const lbm_params& p, Inst* out, double* Lout) {
     I.normal_eps2 = (float)(p.normal_eps * p.normal_eps);
     I.inv_L = (float)(1.0 / L);
     I.inv_Cp = (float)(1.0 / p.Cp);
+    I.buoy_x = (float)(-p.rho_0 * p.beta_T * p.gx);  // Section 4.3, Boussinesq
+    I.buoy_y = (float)(-p.rho_0 * p.beta_T * p.gy);
+    I.T_ref = (float)p.T_ref;
+    if (I.buoy_x != 0.f || I.buoy_y != 0.f) I.flags |= kBuoy;
     *out = I;
     *Lout = L;
 }

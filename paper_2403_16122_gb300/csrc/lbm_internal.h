@@ -20,6 +20,7 @@ enum : int {
     kDirYlo = 1 << 4,
     kDirYhi = 1 << 5,
     kStMask = 1 << 6,
+    kBuoy = 1 << 7,   // Boussinesq force present
 };
 
 // Grouped state layout of one ping-pong buffer of a lattice. Sites are
@@ -70,6 +71,7 @@ struct Inst {
     float tan_w, inv_ramp;
     float normal_eps2;               // squared regularisation of the normal
     float inv_L, inv_Cp;
+    float buoy_x, buoy_y, T_ref;     // F_g = buoy (T - T_ref), buoy = -rho_0 beta g
 };
 
 // One CTA's tile: lattice `inst`, origin (x0, y0), extent tw x th, and the

@@ -192,6 +192,7 @@ struct Phys {
     float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef, tan_w, inv_ramp, eps2;
     float inv_L, inv_Cp;
     float h0ref;   // Cp - (1 - w0) Cp_ref: T-coefficient of the rest h_0 (shifted)
+    float buoy_x, buoy_y, T_ref;
 };
 
 __device__ __forceinline__ Phys load_phys(const Inst& I) {
@@ -203,6 +204,7 @@ __device__ __forceinline__ Phys load_phys(const Inst& I) {
     P.tan_w = I.tan_w; P.inv_ramp = I.inv_ramp; P.eps2 = I.normal_eps2;
     P.inv_L = I.inv_L; P.inv_Cp = I.inv_Cp;
     P.h0ref = I.Cp - (1.f - kW0) * I.Cpref;
+    P.buoy_x = I.buoy_x; P.buoy_y = I.buoy_y; P.T_ref = I.T_ref;
     return P;
 }
 
@@ -379,6 +381,10 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     const float muphi = 4.f * P.beta * (phi - 1.f) * phi * (phi - 0.5f) - P.kappa * lph;
     float Fx = muphi * gphx, Fy = muphi * gphy;
     if (flags & kStMask) { Fx *= (1.f - fs); Fy *= (1.f - fs); }
+    if (flags & kBuoy) {  // Boussinesq buoyancy of Section 4.3 at every site
+        Fx += P.buoy_x * (m.T - P.T_ref);
+        Fy += P.buoy_y * (m.T - P.T_ref);
+    }
 
     // Eqs. 34-35: u* from the flow moments, solid forcing f = -f_s u*
     float mx = 0.f, my = 0.f, fne0 = 0.f;

@@ -34,6 +34,7 @@ BASE = dict(
     rho_l=1.0, rho_ratio_lg=10.0, rho_ratio_sl=0.9, mu_ratio_lg=10.0,
     Ste=0.1, Cp=1.0, Cp_ref=1.0, T_m=0.0, T_w=-1.0,
     theta_deg=90.0, pc_ramp=0.2, normal_eps=1e-3,
+    gx=0.0, gy=0.0, beta_T=0.0, T_ref=0.0, rho_0=1.0,  # Boussinesq force off
 )
 
 
@@ -164,6 +165,26 @@ def bubbles_drop(n=1024, R=None, seed=DEFAULT_SEED, n_bub=8, r_lo=4.0, r_hi=12.0
     bub = place_bubbles(rng, n, n, R, theta, p["W"], n_bub, r_lo, r_hi)
     phi = with_bubbles(phi, bub, p["W"])
     T0 = np.full((n, n), p["T_m"])
+    return p, phi, T0
+
+
+def column_bubbles(l=32, g=1e-4, beta_T=1.0, **over):
+    """Liquid column with three gas bubbles freezing from a cold bottom wall
+    (Section 4.3 geometry: a 4l x 3l box, periodic in x, walls at the bottom
+    and the top; liquid up to 1.8 l; bubbles of radii 0.2 l, 0.24 l, 0.3 l at
+    (l, 0.3 l), (2 l, l), (3 l, 0.4 l)), with the Boussinesq buoyancy
+    F_g = -rho_0 g beta_T (T - T_ref), gravity pointing to -y and T_ref the
+    initial temperature. Thermal properties uniform (one C_p and tau_h)."""
+    nx, ny = 4 * l, 3 * l
+    kw = dict(rho_ratio_lg=10.0, mu_ratio_lg=10.0, rho_ratio_sl=0.9, Ste=0.1)
+    kw.update(over)
+    p = params(nx=nx, ny=ny, periodic_x=1, periodic_y=0, dirichlet_y_lo=1, st_mask_liquid=1,
+               gx=0.0, gy=-g, beta_T=beta_T, rho_0=1.0, **kw)
+    p["T_ref"] = p["T_m"]
+    phi = flat_column(nx, ny, 1.8 * l, p["W"], axis="y")
+    bub = [(1.0 * l, 0.3 * l, 0.2 * l), (2.0 * l, 1.0 * l, 0.24 * l), (3.0 * l, 0.4 * l, 0.3 * l)]
+    phi = with_bubbles(phi, bub, p["W"])
+    T0 = np.full((ny, nx), p["T_m"])
     return p, phi, T0
 
 

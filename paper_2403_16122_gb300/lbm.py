@@ -45,6 +45,9 @@ class lbm_params(ctypes.Structure):
         ("T_m", ctypes.c_double), ("T_w", ctypes.c_double),
         ("theta_deg", ctypes.c_double), ("pc_ramp", ctypes.c_double),
         ("normal_eps", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("beta_T", ctypes.c_double), ("T_ref", ctypes.c_double),
+        ("rho_0", ctypes.c_double),
     ]
 
 

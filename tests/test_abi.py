@@ -43,7 +43,7 @@ def test_params_struct_layout_matches_header():
             fields.append((n.strip(), typ))
     got = [(n, "int32_t" if t is ctypes.c_int32 else "double") for n, t in lbm.lbm_params._fields_]
     assert got == fields
-    assert ctypes.sizeof(lbm.lbm_params) == 10 * 4 + 17 * 8
+    assert ctypes.sizeof(lbm.lbm_params) == 10 * 4 + 22 * 8
 
 
 def test_workspace_size_host_only(lib):

@@ -315,3 +315,24 @@ def test_bulk_phase_field_stays_at_one_while_freezing(oracle_mod):
         worst.append(np.abs(ph - 1.0).max())
     assert max(worst) < 6e-3, worst
     assert worst[-1] < 2e-3, worst
+
+
+@pytest.mark.parametrize("T0", [0.5, -0.25])
+def test_boussinesq_hydrostatic_balance(oracle_mod, T0):
+    """Section 4.3's buoyancy F_g = -rho_0 g beta (T - T_ref) in a closed,
+    single-phase, isothermal column: the fluid comes to rest with the
+    pressure gradient balancing the force, dp/dy = F_g,y (closed form), for
+    either sign of T - T_ref. Liquid everywhere, adiabatic walls, and T above
+    T_m in both cases, so nothing freezes and T stays uniform."""
+    g, beta, rho0, Tref = 1e-3, 1.0, 1.0, 0.0
+    p = inputs.params(nx=8, ny=32, periodic_x=1, periodic_y=0, gx=0.0, gy=-g, beta_T=beta,
+                      T_ref=Tref, rho_0=rho0, T_m=-1.0, T_w=-2.0)
+    o = oracle_mod.Oracle(p).init(np.ones((32, 8)), np.full((32, 8), T0))
+    o.step(20000)
+    f = o.fields()
+    pr = f["p"].mean(axis=1)
+    y = np.arange(4, 28)
+    slope = np.polyfit(y, pr[4:28], 1)[0]
+    expected = -rho0 * (-g) * beta * (T0 - Tref)
+    assert slope == pytest.approx(expected, rel=1e-3)
+    assert np.abs(f["uy"]).max() < 1e-5 and np.abs(f["ux"]).max() < 1e-12
