@@ -392,6 +392,21 @@ def run_ours(args, dist: Dist):
         }
         lat16.close()
 
+    # the Boussinesq option (Section 4.3) on the same lattice: one more force
+    # term per site
+    if forms is not None:
+        pb = dict(p, gy=-1e-4, beta_T=1.0, T_ref=p["T_m"], rho_0=1.0)
+        latb = lbm.Lattice([pb], device=dev)
+        latb.init(phi0, T0)
+        latb.set_kernel(*kernel)
+        latb.step(max(args.warmup, 3))
+        kb = max(1, min(args.steps, 2000))
+        msb = _timed_steps(latb, kb)
+        forms["boussinesq"] = {"value": sites / (msb * 1e-3) / 1e6, "unit": "MLUPS", "steps": kb,
+                               "ms_per_step": msb, "kernel": list(latb.kernel),
+                               "relative_to_plain": ms_per_step / msb}
+        latb.close()
+
     if forms is not None and not args.no_batched:
         forms.update(batched_forms(args, dev, peak))
 

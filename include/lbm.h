@@ -104,6 +104,13 @@ typedef struct lbm_params {
                             force of every site (0 switches it off)          */
     double T_ref;        /* reference temperature of F_g                      */
     double rho_0;        /* reference density of F_g                          */
+    double Cp_ratio_sl;  /* C_p,s / C_p,l (Cp is the liquid's), > 0; with the
+                            next three, per-phase thermal properties mixed by
+                            Eq. 1; all 1: uniform properties                  */
+    double Cp_ratio_gl;  /* C_p,g / C_p,l, > 0                                */
+    double k_ratio_sl;   /* k_s / k_l, > 0: tau_h - 1/2 scales with k, the
+                            liquid's tau_h being tau_h                        */
+    double k_ratio_gl;   /* k_g / k_l, > 0                                    */
 } lbm_params;
 
 /* Observables of the most recent step of an instance (index into the

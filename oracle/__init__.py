@@ -69,6 +69,8 @@ class OracleParams(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double),
         ("beta_T", ctypes.c_double), ("T_ref", ctypes.c_double),
         ("rho_0", ctypes.c_double),
+        ("Cp_ratio_sl", ctypes.c_double), ("Cp_ratio_gl", ctypes.c_double),
+        ("k_ratio_sl", ctypes.c_double), ("k_ratio_gl", ctypes.c_double),
     ]
 
 

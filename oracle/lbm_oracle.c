@@ -172,10 +172,14 @@ void oracle_source_G(double phi, double mdot, double dtx, double dty,
 }
 
 /* Eqs. 8-9 with readings R3/R4: liquid fraction and temperature from H. */
-static void thermal_closure(const oracle_state* s, double H, double* fl, double* T) {
-    double f = clamp01((H - s->Hs) / s->L);               /* Eq. 9a */
-    *fl = f;
-    *T = s->p.T_m + (H - s->Hs - s->L * f) / s->p.Cp;     /* Eq. 9b */
+/* Eq. 9 with the local heat capacity cp of the site (R23: the enthalpy datum
+   is the melting state, H_s = C_p,l T_m and H_l = H_s + L, for every phase;
+   the sensible branches divide by the mixture C_p of Eq. 1). */
+static double liquid_fraction(const oracle_state* s, double H) {
+    return clamp01((H - s->Hs) / s->L);                   /* Eq. 9a */
+}
+static double temperature(const oracle_state* s, double H, double fl, double cp) {
+    return s->p.T_m + (H - s->Hs - s->L * fl) / cp;       /* Eq. 9b */
 }
 
 /* R3: solid only in the liquid content of a site. */
@@ -184,17 +188,29 @@ static double solid_fraction(const oracle_state* s, double fl, double phihat) {
     return chi * (1.0 - fl);
 }
 
-void oracle_closure(const oracle_state* s, double H, double phihat, double* fs,
-                    double* T) {
-    double fl;
-    thermal_closure(s, H, &fl, T);
-    *fs = solid_fraction(s, fl, phihat);
-}
-
 /* Eq. 1 (reading R2: phi clamped to [0, 1]). */
 static double mix(double fs, double phi, double zs, double zl, double zg) {
     double ph = clamp01(phi);
     return fs * zs + (1.0 - fs) * ph * zl + (1.0 - fs) * (1.0 - ph) * zg;
+}
+
+/* Local heat capacity and enthalpy relaxation time (Eq. 1 for C_p and k;
+   R23: tau_h - 1/2 proportional to k, the liquid's given by tau_h). */
+static double heat_capacity(const oracle_state* s, double fs, double phi) {
+    const oracle_params* p = &s->p;
+    return mix(fs, phi, p->Cp * p->Cp_ratio_sl, p->Cp, p->Cp * p->Cp_ratio_gl);
+}
+static double tau_enthalpy(const oracle_state* s, double fs, double phi) {
+    const oracle_params* p = &s->p;
+    return mix(fs, phi, p->k_ratio_sl, 1.0, p->k_ratio_gl) * (p->tau_h - 0.5) + 0.5;
+}
+
+/* Pointwise closure for tests: phihat stands in for phi in the mixture. */
+void oracle_closure(const oracle_state* s, double H, double phihat, double* fs,
+                    double* T) {
+    double fl = liquid_fraction(s, H);
+    *fs = solid_fraction(s, fl, phihat);
+    *T = temperature(s, H, fl, heat_capacity(s, *fs, phihat));
 }
 
 /* ---------------------------------------------------------------------- */
@@ -309,6 +325,8 @@ static int valid(const oracle_params* p) {
     if (!(p->theta_deg > 0 && p->theta_deg < 180)) return 0;
     if (!(p->pc_ramp > 0)) return 0;
     if (!(p->normal_eps > 0)) return 0;
+    if (!(p->Cp_ratio_sl > 0) || !(p->Cp_ratio_gl > 0)) return 0;
+    if (!(p->k_ratio_sl > 0) || !(p->k_ratio_gl > 0)) return 0;
     return 1;
 }
 
@@ -363,19 +381,20 @@ void oracle_derived(const oracle_state* s, double* o) {
 
 /* Start at rest (u = 0, p = 0) with the distributions at equilibrium. The
    material is liquid-like before freezing starts (f_l = 1), so
-   H = Cp T0 + L (Eq. 8). */
+   H = H_l + C_p (T0 - T_m) (Eq. 8) with C_p the mixture of liquid and gas. */
 int oracle_init(oracle_state* s, const double* phi0, const double* T0) {
     const int64_t n = s->n;
     double eq[9];
     for (int64_t k = 0; k < n; ++k) {
-        double H = s->p.Cp * T0[k] + s->L;
-        double fl, T;
-        thermal_closure(s, H, &fl, &T);
+        double cp0 = heat_capacity(s, 0.0, phi0[k]);
+        double H = s->Hl + cp0 * (T0[k] - s->p.T_m);
+        double fl = liquid_fraction(s, H);
         double fs = solid_fraction(s, fl, phi0[k]);
+        double T = temperature(s, H, fl, heat_capacity(s, fs, phi0[k]));
         double rho = mix(fs, phi0[k], s->rho_s, s->p.rho_l, s->rho_g);
         oracle_geq(phi0[k], 0.0, 0.0, eq);
         for (int i = 0; i < 9; ++i) s->pop[(SET_G * 9 + i) * n + k] = eq[i];
-        oracle_heq(H, T, s->p.Cp, s->p.Cp_ref, 0.0, 0.0, eq);
+        oracle_heq(H, T, heat_capacity(s, fs, phi0[k]), s->p.Cp_ref, 0.0, 0.0, eq);
         for (int i = 0; i < 9; ++i) s->pop[(SET_H * 9 + i) * n + k] = eq[i];
         oracle_feq(0.0, rho, 0.0, 0.0, eq);
         for (int i = 0; i < 9; ++i) s->pop[(SET_F * 9 + i) * n + k] = eq[i];
@@ -440,12 +459,12 @@ static void step_once(oracle_state* s) {
                 H += s->pre[(SET_H * 9 + i) * n + k];      /* Eq. 29 */
                 phihat += s->pre[(SET_G * 9 + i) * n + k];
             }
-            double fl, T;
-            thermal_closure(s, H, &fl, &T);                /* Eqs. 8-9, R3 */
+            double fl = liquid_fraction(s, H);             /* Eq. 9a, R3 */
             double chi = clamp01((phihat - 0.5) / p->pc_ramp + 0.5);
             double fs = chi * (1.0 - fl);
             double mdot = (1.0 - s->rho_s / p->rho_l) * chi * (fl_prev[k] - fl); /* Eq. 19, R6 */
             double ph = phihat / (1.0 - 0.5 * mdot);     /* Eq. 26, R5 */
+            double T = temperature(s, H, fl, heat_capacity(s, fs, ph));  /* Eq. 9b, R23 */
             Hf[k] = H;
             Tf[k] = T;
             fsf[k] = fs;
@@ -522,11 +541,12 @@ static void step_once(oracle_state* s) {
 
             /* Enthalpy (Eqs. 27-28). */
             double heq[9];
-            oracle_heq(H, T, p->Cp, p->Cp_ref, ux, uy, heq);
+            oracle_heq(H, T, heat_capacity(s, fs, ph), p->Cp_ref, ux, uy, heq);
+            const double tau_h = tau_enthalpy(s, fs, ph);
             const double* hpre = s->pre + (int64_t)(SET_H * 9) * n;
             for (int i = 0; i < 9; ++i) {
                 double hi = hpre[i * n + k];
-                s->pop_new[(int64_t)(SET_H * 9 + i) * n + k] = hi - (hi - heq[i]) / p->tau_h;
+                s->pop_new[(int64_t)(SET_H * 9 + i) * n + k] = hi - (hi - heq[i]) / tau_h;
             }
 
             /* Flow (Eqs. 30-33). */

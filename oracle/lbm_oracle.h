@@ -59,6 +59,10 @@ typedef struct oracle_params {
     double beta_T;         /* volumetric expansion coefficient beta               */
     double T_ref;          /* reference temperature of the Boussinesq force       */
     double rho_0;          /* reference density rho_0 of the Boussinesq force     */
+    double Cp_ratio_sl;    /* C_p,s / C_p,l (Section 4.2: 0.5); 1 = uniform       */
+    double Cp_ratio_gl;    /* C_p,g / C_p,l                                       */
+    double k_ratio_sl;     /* k_s / k_l (Section 4.2: 3.8); 1 = uniform           */
+    double k_ratio_gl;     /* k_g / k_l                                           */
 } oracle_params;
 
 /* Observables of the most recent step (indices into the output array). */

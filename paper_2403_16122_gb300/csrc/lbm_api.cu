@@ -52,6 +52,10 @@ bool valid_params(const lbm_params& p) {
     if (!isfinite(p.gx) || !isfinite(p.gy) || !isfinite(p.beta_T) || !isfinite(p.T_ref) ||
         !isfinite(p.rho_0))
         return false;
+    if (!(p.Cp_ratio_sl > 0) || !(p.Cp_ratio_gl > 0) || !(p.k_ratio_sl > 0) ||
+        !(p.k_ratio_gl > 0) || !isfinite(p.Cp_ratio_sl) || !isfinite(p.Cp_ratio_gl) ||
+        !isfinite(p.k_ratio_sl) || !isfinite(p.k_ratio_gl))
+        return false;
     return true;
 }
 
@@ -434,6 +438,8 @@ int lbm_init_fields(lbm_handle* h, int32_t inst, const double* phi0, const doubl
     c.Cp = p.Cp;
     c.Cpref = p.Cp_ref;
     c.inv_ramp = 1.0 / p.pc_ramp;
+    c.Cp_s = p.Cp * p.Cp_ratio_sl;
+    c.Cp_g = p.Cp * p.Cp_ratio_gl;
     e = lbmk::launch_init(h->d_inst, inst, (int)n, h->storage, c, h->d_stage,
                           h->d_stage + h->layout.max_sites, h->parity, h->stream);
     h->launches++;
@@ -650,7 +656,14 @@ int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double
         double fl = (H - Hs) / L;
         fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
         phr[k] = (float)phi;
-        Tr[k] = (float)(p.T_m + (H - Hs - L * fl) / p.Cp);
+        // Eq. 9b with the local heat capacity (Eq. 1; uniform: Cp)
+        const double ph = phi < 0 ? 0 : (phi > 1 ? 1 : phi);
+        double chi = (phi - 0.5) / p.pc_ramp + 0.5;
+        chi = chi < 0 ? 0 : (chi > 1 ? 1 : chi);
+        const double fs = chi * (1.0 - fl);
+        const double cp = fs * p.Cp * p.Cp_ratio_sl +
+                          (1.0 - fs) * (ph * p.Cp + (1.0 - ph) * p.Cp * p.Cp_ratio_gl);
+        Tr[k] = (float)(p.T_m + (H - Hs - L * fl) / cp);
     }
     std::vector<__half> tp((size_t)27 * n);
     for (int y = 0; y < p.ny; ++y)
@@ -900,6 +913,14 @@ void inst_from_params(const lbm_params& p, Inst* out, double* Lout) {
     I.buoy_y = (float)(-p.rho_0 * p.beta_T * p.gy);
     I.T_ref = (float)p.T_ref;
     if (I.buoy_x != 0.f || I.buoy_y != 0.f) I.flags |= kBuoy;
+    // per-phase thermal properties (Eq. 1 for C_p and k; tau_h - 1/2 ~ k)
+    I.Cp_s = (float)(p.Cp * p.Cp_ratio_sl);
+    I.Cp_g = (float)(p.Cp * p.Cp_ratio_gl);
+    I.k_s = (float)p.k_ratio_sl;
+    I.k_g = (float)p.k_ratio_gl;
+    I.dtau_h = (float)(p.tau_h - 0.5);
+    if (p.Cp_ratio_sl != 1.0 || p.Cp_ratio_gl != 1.0 || p.k_ratio_sl != 1.0 || p.k_ratio_gl != 1.0)
+        I.flags |= kPhaseProps;
     *out = I;
     *Lout = L;
 }

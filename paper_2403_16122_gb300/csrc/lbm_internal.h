@@ -21,6 +21,7 @@ enum : int {
     kDirYhi = 1 << 5,
     kStMask = 1 << 6,
     kBuoy = 1 << 7,   // Boussinesq force present
+    kPhaseProps = 1 << 8,  // per-phase heat capacity / conductivity
 };
 
 // Grouped state layout of one ping-pong buffer of a lattice. Sites are
@@ -72,6 +73,9 @@ struct Inst {
     float normal_eps2;               // squared regularisation of the normal
     float inv_L, inv_Cp;
     float buoy_x, buoy_y, T_ref;     // F_g = buoy (T - T_ref), buoy = -rho_0 beta g
+    float Cp_s, Cp_g;                // heat capacities of solid and gas (liquid: Cp)
+    float k_s, k_g;                  // conductivities relative to the liquid's
+    float dtau_h;                    // tau_h - 1/2 of the liquid
 };
 
 // One CTA's tile: lattice `inst`, origin (x0, y0), extent tw x th, and the
@@ -144,6 +148,7 @@ cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partia
 // Double-precision constants of the equilibrium initialisation.
 struct InitConst {
     double L, Hs, Hl, Tm, Cp, Cpref, inv_ramp;
+    double Cp_s, Cp_g;  // per-phase heat capacities (equal to Cp when uniform)
 };
 
 // Equilibrium initialisation of lattice `inst` (nx*ny sites) from phi0/T0

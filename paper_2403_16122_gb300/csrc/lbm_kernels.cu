@@ -193,6 +193,8 @@ struct Phys {
     float inv_L, inv_Cp;
     float h0ref;   // Cp - (1 - w0) Cp_ref: T-coefficient of the rest h_0 (shifted)
     float buoy_x, buoy_y, T_ref;
+    float Cp_s, Cp_g, k_s, k_g, dtau_h;
+    bool phase_props;
 };
 
 __device__ __forceinline__ Phys load_phys(const Inst& I) {
@@ -205,6 +207,8 @@ __device__ __forceinline__ Phys load_phys(const Inst& I) {
     P.inv_L = I.inv_L; P.inv_Cp = I.inv_Cp;
     P.h0ref = I.Cp - (1.f - kW0) * I.Cpref;
     P.buoy_x = I.buoy_x; P.buoy_y = I.buoy_y; P.T_ref = I.T_ref;
+    P.Cp_s = I.Cp_s; P.Cp_g = I.Cp_g; P.k_s = I.k_s; P.k_g = I.k_g; P.dtau_h = I.dtau_h;
+    P.phase_props = (I.flags & kPhaseProps) != 0;
     return P;
 }
 
@@ -237,7 +241,12 @@ __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], co
     // Eq. 9b on the shifted enthalpy, H - H_s - L f_l = H' - H_s + L (f_l^{n-1}
     // - f_l); inside the mushy range the exact value is T_m (evaluating the sum
     // there would only add the rounding of f_l times L)
-    m.T = m.mushy ? P.Tm : P.Tm + (Hp - P.Hs + P.L * (flp - fl)) * P.inv_Cp;
+    if (P.phase_props) {  // sensible branches with the local C_p of Eq. 1
+        const float cp = mix3(fs, phi, P.Cp_s, P.Cp, P.Cp_g);
+        m.T = m.mushy ? P.Tm : P.Tm + (Hp - P.Hs + P.L * (flp - fl)) / cp;
+    } else {
+        m.T = m.mushy ? P.Tm : P.Tm + (Hp - P.Hs + P.L * (flp - fl)) * P.inv_Cp;
+    }
     return m;
 }
 
@@ -433,7 +442,13 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     const float T = m.T;
 
     const float fsrc = 1.f - 0.5f * omega_f;
-    const float TCp = T * P.Cp, TCpref = T * P.Cpref;
+    // per-phase properties: local C_p in h^eq, tau_h - 1/2 scaled by k / k_l
+    float Cp_loc = P.Cp, omega_h = P.omega_h;
+    if (P.phase_props) {
+        Cp_loc = mix3(fs, phi, P.Cp_s, P.Cp, P.Cp_g);
+        omega_h = 1.f / (mix3(fs, phi, P.k_s, 1.f, P.k_g) * P.dtau_h + 0.5f);
+    }
+    const float TCp = T * Cp_loc, TCpref = T * P.Cpref;
     const float uu15 = 1.5f * uu;
     float g0n = 0.f, h0n = 0.f, f0n = 0.f;  // rest populations
     float eg = 0.f, eh = 0.f, ef = 0.f;     // FP16 storage: rounding carried to them
@@ -452,10 +467,10 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         float hn;
         if (i == 0) {
             const float heq0 = m.Hp + dL - TCpref + kW0 * (TCpref - TCp * uu15);
-            hn = (1.f - P.omega_h) * (hi + dL) + P.omega_h * heq0;
+            hn = (1.f - omega_h) * (hi + dL) + omega_h * heq0;
         } else {
             const float heq = w * TCpref + TCp * si;
-            hn = hi - P.omega_h * (hi - heq);
+            hn = hi - omega_h * (hi - heq);
         }
         // f (Eqs. 30-33)
         const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
@@ -1353,6 +1368,33 @@ __global__ void barrier_timeout_probe(unsigned* bar, int* err, unsigned long lon
 // ---------------------------------------------------------------------------
 // Initialisation (double precision, then rounded to the storage format)
 // ---------------------------------------------------------------------------
+// Start of a site: liquid-like before freezing (f_l = 1), so H = H_l + C_p
+// (T0 - T_m) with C_p the liquid/gas mixture of Eq. 1, then Eq. 9 back with
+// the local C_p of the resulting state (uniform properties: C_p itself).
+struct InitSite {
+    double H, fl, T;
+};
+__device__ __forceinline__ InitSite init_site(const InitConst& c, double phi, double T0) {
+    InitSite r;
+    if (c.Cp_s == c.Cp && c.Cp_g == c.Cp) {
+        r.H = c.Cp * T0 + c.L;
+        double fl = (r.H - c.Hs) / c.L;                         // Eq. 9a
+        r.fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
+        r.T = c.Tm + (r.H - c.Hs - c.L * r.fl) / c.Cp;          // Eq. 9b
+        return r;
+    }
+    const double ph = phi < 0 ? 0 : (phi > 1 ? 1 : phi);
+    r.H = c.Hl + (ph * c.Cp + (1.0 - ph) * c.Cp_g) * (T0 - c.Tm);
+    double fl = (r.H - c.Hs) / c.L;
+    r.fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
+    double chi = (phi - 0.5) * c.inv_ramp + 0.5;
+    chi = chi < 0 ? 0 : (chi > 1 ? 1 : chi);
+    const double fs = chi * (1.0 - r.fl);
+    const double cp = fs * c.Cp_s + (1.0 - fs) * (ph * c.Cp + (1.0 - ph) * c.Cp_g);
+    r.T = c.Tm + (r.H - c.Hs - c.L * r.fl) / cp;
+    return r;
+}
+
 __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
                           const double* __restrict__ phi0, const double* __restrict__ T0,
                           int parity) {
@@ -1362,10 +1404,8 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
         const int x = k % I.nx, y = k / I.nx;
         const long long idx = (long long)y * I.pitch + x;
         const double ph = phi0[k];
-        const double H = c.Cp * T0[k] + c.L;
-        double fl = (H - c.Hs) / c.L;                 // Eq. 9a
-        fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
-        const double T = c.Tm + (H - c.Hs - c.L * fl) / c.Cp;  // Eq. 9b
+        const InitSite st = init_site(c, ph, T0[k]);
+        const double H = st.H, fl = st.fl, T = st.T;
         float* P = static_cast<float*>(I.pop[parity]);
         float* A = I.aux[parity];
         const int plane = (int)I.plane, site = (int)idx;
@@ -1392,11 +1432,8 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
 
 // FP16 storage: the same equilibrium start, each population stored as its
 // deviation from the rest-equilibrium reference of the site it streams into.
-__device__ __forceinline__ double init_T(const InitConst& c, double T0) {
-    const double H = c.Cp * T0 + c.L;
-    double fl = (H - c.Hs) / c.L;
-    fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
-    return c.Tm + (H - c.Hs - c.L * fl) / c.Cp;
+__device__ __forceinline__ double init_T(const InitConst& c, double phi, double T0) {
+    return init_site(c, phi, T0).T;
 }
 
 __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
@@ -1409,10 +1446,8 @@ __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
         const int x = k % I.nx, y = k / I.nx;
         const int idx = y * I.pitch + x;
         const double ph = phi0[k];
-        const double H = c.Cp * T0[k] + c.L;
-        double fl = (H - c.Hs) / c.L;
-        fl = fl < 0 ? 0 : (fl > 1 ? 1 : fl);
-        const double T = c.Tm + (H - c.Hs - c.L * fl) / c.Cp;
+        const InitSite st = init_site(c, ph, T0[k]);
+        const double H = st.H, fl = st.fl, T = st.T;
         __half* P = static_cast<__half*>(I.pop[parity]);
         float* A = I.aux[parity];
         const float phr = (float)ph, Tr = (float)T;
@@ -1430,7 +1465,7 @@ __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
             }
             const int kd = wall ? k : yd * I.nx + xd;
             const float phd = (float)phi0[kd];
-            const float Td = (float)init_T(c, T0[kd]);
+            const float Td = (float)init_T(c, phi0[kd], T0[kd]);
             if (i == 0) {  // rest populations in FP32
                 A[own0_at(idx, 0)] = (float)(w * ph);                                 // Eq. 24
                 A[own0_at(idx, 1)] =

@@ -35,6 +35,7 @@ BASE = dict(
     Ste=0.1, Cp=1.0, Cp_ref=1.0, T_m=0.0, T_w=-1.0,
     theta_deg=90.0, pc_ramp=0.2, normal_eps=1e-3,
     gx=0.0, gy=0.0, beta_T=0.0, T_ref=0.0, rho_0=1.0,  # Boussinesq force off
+    Cp_ratio_sl=1.0, Cp_ratio_gl=1.0, k_ratio_sl=1.0, k_ratio_gl=1.0,  # uniform thermal props
 )
 
 

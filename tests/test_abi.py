@@ -43,7 +43,7 @@ def test_params_struct_layout_matches_header():
             fields.append((n.strip(), typ))
     got = [(n, "int32_t" if t is ctypes.c_int32 else "double") for n, t in lbm.lbm_params._fields_]
     assert got == fields
-    assert ctypes.sizeof(lbm.lbm_params) == 10 * 4 + 22 * 8
+    assert ctypes.sizeof(lbm.lbm_params) == 10 * 4 + 26 * 8
 
 
 def test_workspace_size_host_only(lib):
@@ -59,7 +59,9 @@ def test_workspace_size_host_only(lib):
 
 @pytest.mark.parametrize("bad", [dict(nx=2), dict(tau_h=0.5), dict(mobility=0.0),
                                  dict(theta_deg=0.0), dict(T_w=0.5), dict(Ste=-1.0),
-                                 dict(pc_ramp=0.0), dict(periodic_x=2), dict(normal_eps=0.0)])
+                                 dict(pc_ramp=0.0), dict(periodic_x=2), dict(normal_eps=0.0),
+                                 dict(k_ratio_sl=0.0), dict(Cp_ratio_gl=-1.0),
+                                 dict(beta_T=float("inf"))])
 def test_invalid_parameters_rejected(lib, bad):
     p = inputs.params(**bad)
     with pytest.raises(lbm.LbmError) as e:

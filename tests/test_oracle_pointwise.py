@@ -286,6 +286,7 @@ def test_derived_parameters(oracle_mod):
 
 def test_invalid_parameters_rejected(oracle_mod):
     for bad in (dict(nx=2), dict(tau_h=0.5), dict(mobility=0.0), dict(theta_deg=180.0),
-                dict(T_w=0.0), dict(Ste=0.0), dict(rho_ratio_lg=-1.0), dict(normal_eps=0.0)):
+                dict(T_w=0.0), dict(Ste=0.0), dict(rho_ratio_lg=-1.0), dict(normal_eps=0.0),
+                dict(k_ratio_gl=0.0), dict(Cp_ratio_sl=-0.5)):
         with pytest.raises(oracle_mod.OracleError):
             _state(oracle_mod, **bad)

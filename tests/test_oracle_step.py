@@ -126,6 +126,51 @@ def test_thermal_diffusivity_from_tau_h(oracle_mod):
     assert rate == pytest.approx(CS2 * 0.4 * k * k, rel=0.01)
 
 
+@pytest.mark.parametrize("phase", ["gas", "solid"])
+def test_thermal_diffusivity_of_each_phase(oracle_mod, phase):
+    """Per-phase properties (Eq. 1 for C_p and k; R23): in a pure phase the
+    enthalpy equation C_p dT/dt = alpha C_p,ref lap T with alpha = c_s^2
+    (tau_h - 1/2) and tau_h - 1/2 scaled by k / k_l makes a temperature wave
+    decay at alpha C_p,ref / C_p k^2. Gas: phi = 0 above T_m; solid: phi = 1
+    below T_m, started from its equilibrium state (f_l = 0)."""
+    nx, ny = 64, 4
+    cp_r, k_r = (0.5, 0.2) if phase == "gas" else (0.5, 3.8)
+    key = "gl" if phase == "gas" else "sl"
+    p = inputs.params(nx=nx, ny=ny, tau_h=0.6,
+                      **{f"Cp_ratio_{key}": cp_r, f"k_ratio_{key}": k_r})
+    x, _ = inputs.coords(nx, ny)
+    k = 2 * math.pi / nx
+    basis = np.sin(k * x)
+    if phase == "gas":
+        Tbar = 1.0
+        o = run(oracle_mod, p, np.zeros((ny, nx)), Tbar + 0.2 * basis)
+    else:
+        Tbar = p["T_m"] - 0.5
+        T = Tbar + 0.2 * basis
+        o = run(oracle_mod, p, np.ones((ny, nx)), np.full((ny, nx), 1.0))
+        cps = p["Cp"] * cp_r
+        L = p["Cp"] * (p["T_m"] - p["T_w"]) / p["Ste"]
+        pops = np.zeros((27, ny, nx))
+        aux = np.zeros((5, ny, nx))
+        rho_s = p["rho_l"] * p["rho_ratio_sl"]
+        for (yy, xx), Tv in np.ndenumerate(T):
+            H = p["Cp"] * p["T_m"] + cps * (Tv - p["T_m"])   # solid branch of Eq. 9
+            pops[0:9, yy, xx] = oracle_mod.geq(1.0, 0.0, 0.0)
+            pops[9:18, yy, xx] = oracle_mod.heq(H, Tv, cps, p["Cp_ref"], 0.0, 0.0)
+            pops[18:27, yy, xx] = oracle_mod.feq(0.0, rho_s, 0.0, 0.0)
+        o.set_state(pops, aux)
+        o.step(1)
+        assert np.abs(o.fields()["fs"] - 1.0).max() < 1e-12
+        assert L > 0
+    o.step(50)
+    a1 = _mode_amplitude(o.fields()["T"] - Tbar, basis)
+    o.step(1500)
+    a2 = _mode_amplitude(o.fields()["T"] - Tbar, basis)
+    rate = math.log(a1 / a2) / 1500
+    alpha = CS2 * k_r * (0.6 - 0.5)
+    assert rate == pytest.approx(alpha * p["Cp_ref"] / (p["Cp"] * cp_r) * k * k, rel=0.01)
+
+
 def test_dirichlet_wall_conduction(oracle_mod):
     """Gas between two cold walls at half-links x = -1/2 and x = nx - 1/2 with a
     negligible latent heat (Ste = 1e5): the slowest mode sin(pi (x + 1/2) / nx)
