@@ -274,19 +274,32 @@ def test_per_phase_thermal_properties(oracle_mod):
     """Per-phase heat capacity and conductivity (Eq. 1 for C_p and k; the
     droplet cases of Section 4.2 use C_p,s/C_p,l = 0.5 and k_s/k_l = 3.8; the
     gas keeps the liquid's C_p, as one of the paper's figure captions states,
-    and k_g/k_l = 0.04, a reading of "much lower"): a sessile drop freezing
-    for 1000 steps, staged strips and tiles against the oracle."""
+    and k_g/k_l = 0.04, a reading of "much lower"): a sessile drop freezing,
+    staged strips and tiles against the oracle. The contact line makes this
+    case far less well conditioned than the uniform one: in the oracle itself
+    a relative perturbation of 1e-7 (FP32 rounding) of the state grows to 5e-6
+    in h_0 over 1000 steps, and rounding enters every step, so the
+    distributions are held to 1e-5 after 100 steps and the observables to
+    1e-5 relative after 1000."""
     from paper_2403_16122_gb300 import lbm
 
     p, phi0, T0 = inputs.sessile(nx=96, ny=64, R=24.0, theta_deg=100.0, Cp_ratio_sl=0.5,
                                  k_ratio_sl=3.8, Cp_ratio_gl=1.0, k_ratio_gl=0.04)
-    o = oracle_run(oracle_mod, p, phi0, T0, 1000)
+    o = oracle_run(oracle_mod, p, phi0, T0, 100)
+    lats = []
     for kern in (None, (lbm.LBM_KERNEL_TILE, 32, 8)):
         lat = gpu_run([p], [(phi0, T0)], 0)
         if kern:
             lat.set_kernel(*kern)
-        lat.step(1000)
+        lat.step(100)
         compare_state(lat.get_state(), o.get_state())
+        lats.append(lat)
+    o.step(900)
+    want = o.observables()
+    for lat in lats:
+        got = lat.step(900).observables()
+        for k in ("volume", "solid", "enthalpy", "solid_col"):
+            assert got[k] == pytest.approx(want[k], rel=1e-5), k
     # the properties matter: uniform ones freeze a different amount
     q = dict(p, Cp_ratio_sl=1.0, k_ratio_sl=1.0, Cp_ratio_gl=1.0, k_ratio_gl=1.0)
     o1 = oracle_run(oracle_mod, q, phi0, T0, 1000)
