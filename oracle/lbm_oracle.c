@@ -57,6 +57,11 @@
  *   R14 Dirichlet walls use anti-bounce-back for h:
  *       h_i = -h_ibar^* + 2 w_i Cp_ref T_w ; no-flux (g) and no-slip (f) walls
  *       use half-way bounce-back (Section 4.1).
+ *   R22 The Boussinesq force of Section 4.3, F_g = -rho_0 g beta (T - T_ref),
+ *       joins F at every site with the step's T (zero unless g, beta given).
+ *   R23 Per-phase C_p and k mix by Eq. 1; tau_h - 1/2 scales with k / k_l;
+ *       Eq. 9 keeps the melting-state datum (H_s = C_p,l T_m, H_l = H_s + L)
+ *       and divides the sensible enthalpy by the local C_p.
  *   Parity unpinned (no closed form separates the alternatives; the choice
  *   defines the scheme): R7, R9, R12, the ramp width of R3 and the eps of R8.
  *   The carried planes are f_l, (phi u)_x, (phi u)_y, p, S.
