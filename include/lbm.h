@@ -208,6 +208,16 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
 #define LBM_KERNEL_STRIP  1
 #define LBM_KERNEL_STAGED 2
 
+/* Thermal type of the walls of lattice `inst` from now on (1 = held at T_w,
+   0 = adiabatic; flags as in lbm_params). The paper relaxes a drop to its
+   contact angle without cooling and then cools the substrate (Sections 4.2,
+   4.3): step with the walls adiabatic, switch them here, keep stepping; the
+   state, the latent heat (set by T_w and Ste) and every other parameter are
+   untouched. Periodic directions have no walls (their flags must be 0).
+   Synchronises the stream; drops captured graphs. LBM_EINVAL otherwise. */
+int lbm_set_thermal_walls(lbm_handle* h, int32_t inst, int32_t x_lo, int32_t x_hi,
+                          int32_t y_lo, int32_t y_hi);
+
 /* Select the kernel layout (host tables are rebuilt and uploaded on the
    stream; synchronises it). LBM_EINVAL for an unsupported combination. */
 int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c);

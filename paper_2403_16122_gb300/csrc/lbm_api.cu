@@ -728,6 +728,25 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double*
     return LBM_OK;
 }
 
+int lbm_set_thermal_walls(lbm_handle* h, int32_t inst, int32_t x_lo, int32_t x_hi,
+                          int32_t y_lo, int32_t y_hi) {
+    if (!inst_ok(h, inst)) return LBM_EINVAL;
+    const int32_t v[4] = {x_lo, x_hi, y_lo, y_hi};
+    for (int32_t f : v)
+        if (f != 0 && f != 1) return LBM_EINVAL;
+    lbm_params& p = h->params[inst];
+    if ((p.periodic_x && (x_lo || x_hi)) || (p.periodic_y && (y_lo || y_hi))) return LBM_EINVAL;
+    p.dirichlet_x_lo = x_lo;
+    p.dirichlet_x_hi = x_hi;
+    p.dirichlet_y_lo = y_lo;
+    p.dirichlet_y_hi = y_hi;
+    const int keep = lbmk::kDirXlo | lbmk::kDirXhi | lbmk::kDirYlo | lbmk::kDirYhi;
+    h->inst[inst].flags = (h->inst[inst].flags & ~keep) | (x_lo ? lbmk::kDirXlo : 0) |
+                          (x_hi ? lbmk::kDirXhi : 0) | (y_lo ? lbmk::kDirYlo : 0) |
+                          (y_hi ? lbmk::kDirYhi : 0);
+    return upload_tables(h);  // instance table, item tables; drops graphs; synchronises
+}
+
 int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c) {
     if (!h) return LBM_EINVAL;
     if (kind == LBM_KERNEL_TILE) {

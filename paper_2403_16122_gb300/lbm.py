@@ -68,7 +68,7 @@ SYMBOLS = (
     "lbm_observables", "lbm_observables_all", "lbm_get_state", "lbm_set_state",
     "lbm_step_count", "lbm_launch_count", "lbm_destroy", "lbm_error_string",
     "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune", "lbm_step_noalloc",
-    "lbm_set_exec", "lbm_get_exec", "lbm_barrier_selftest",
+    "lbm_set_exec", "lbm_get_exec", "lbm_barrier_selftest", "lbm_set_thermal_walls",
 )
 LBM_KERNEL_TILE, LBM_KERNEL_STRIP, LBM_KERNEL_STAGED = 0, 1, 2
 LBM_EXEC_LAUNCH, LBM_EXEC_GRAPH, LBM_EXEC_PERSISTENT = 0, 1, 2
@@ -113,6 +113,7 @@ def load(path: str | None = None):
         lib.lbm_set_exec.argtypes = [vp, i32, i32]
         lib.lbm_get_exec.argtypes = [vp, P(i32)]
         lib.lbm_barrier_selftest.argtypes = [vp, u64, P(i32)]
+        lib.lbm_set_thermal_walls.argtypes = [vp, i32, i32, i32, i32, i32]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in ("lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
@@ -269,6 +270,12 @@ def lbm_get_exec(h):
     return tuple(out[:])
 
 
+def lbm_set_thermal_walls(h, inst: int, x_lo: int, x_hi: int, y_lo: int, y_hi: int):
+    rc = load().lbm_set_thermal_walls(h, int(inst), int(x_lo), int(x_hi), int(y_lo), int(y_hi))
+    if rc:
+        raise LbmError(rc, "lbm_set_thermal_walls")
+
+
 def lbm_barrier_selftest(h, limit_ns: int) -> int:
     flag = ctypes.c_int32()
     rc = load().lbm_barrier_selftest(h, ctypes.c_uint64(int(limit_ns)), ctypes.byref(flag))
@@ -350,6 +357,15 @@ class Lattice:
 
     def autotune(self, steps: int = 20):
         return lbm_autotune(self._h, steps)
+
+    def set_thermal_walls(self, x_lo=0, x_hi=0, y_lo=0, y_hi=0, inst: int = 0):
+        """Switch the thermal wall types of one lattice (for example from
+        adiabatic during the isothermal relaxation to the contact angle to a
+        cold substrate)."""
+        lbm_set_thermal_walls(self._h, inst, x_lo, x_hi, y_lo, y_hi)
+        self.params[inst].update(dirichlet_x_lo=x_lo, dirichlet_x_hi=x_hi,
+                                 dirichlet_y_lo=y_lo, dirichlet_y_hi=y_hi)
+        return self
 
     def set_exec(self, mode: int, chunk: int = 64):
         lbm_set_exec(self._h, mode, chunk)

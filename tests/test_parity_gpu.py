@@ -304,3 +304,27 @@ def test_per_phase_thermal_properties(oracle_mod):
     q = dict(p, Cp_ratio_sl=1.0, k_ratio_sl=1.0, Cp_ratio_gl=1.0, k_ratio_gl=1.0)
     o1 = oracle_run(oracle_mod, q, phi0, T0, 1000)
     assert abs(o.observables()["solid"] - o1.observables()["solid"]) > 1.0
+
+
+def test_relax_then_cool(oracle_mod):
+    """The paper's protocol (Sections 4.2, 4.3): the drop first relaxes to its
+    contact angle with adiabatic walls (nothing freezes), then the substrate
+    is switched to the cold wall temperature in place
+    (lbm_set_thermal_walls) and freezing starts; against the oracle run with
+    the same two phases (state carried over between two oracle instances)."""
+    from paper_2403_16122_gb300 import lbm
+
+    p_cool, phi0, T0 = inputs.sessile(nx=96, ny=64, R=24.0, theta_deg=60.0)
+    p_relax = dict(p_cool, dirichlet_y_lo=0)
+    o = oracle_run(oracle_mod, p_relax, phi0, T0, 300)
+    assert o.observables()["solid"] == 0.0
+    o2 = oracle_mod.Oracle(p_cool).init(phi0, T0)
+    o2.set_state(*o.get_state())
+    o2.step(700)
+    lat = gpu_run([p_relax], [(phi0, T0)], 300)
+    assert lat.observables()["solid"] == 0.0
+    with pytest.raises(lbm.LbmError):
+        lat.set_thermal_walls(x_lo=1)  # periodic in x: no such wall
+    lat.set_thermal_walls(y_lo=1).step(700)
+    compare_state(lat.get_state(), o2.get_state())
+    assert lat.observables()["solid"] > 1.0
