@@ -187,6 +187,7 @@ void fill_inst(lbm_handle* h, int k) {
     Inst I;
     double L = 0.0;
     lbmk::inst_from_params(p, &I, &L);
+    I.part_stride = h->layout.max_parts;
     for (int b = 0; b < 2; ++b) {
         I.pop[b] = h->ws + h->layout.pop_off[b][k];
         I.aux[b] = reinterpret_cast<float*>(h->ws + h->layout.aux_off[b][k]);

@@ -64,6 +64,7 @@ struct Inst {
     void* pop[2];             // population regions, ping-pong buffers
     float* aux[2];            // own-site regions
     int part_begin, part_end; // observable partials of this lattice's tiles
+    int part_stride;          // partials are observable-major: [kObs][part_stride]
     // physics, single precision
     float L, Hs, Tm, Cp, Cpref, Tw;
     float omega_g, omega_h;          // 1 / tau

@@ -253,8 +253,10 @@ __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], co
 // ---------------------------------------------------------------------------
 // Block reduction of the observables (FP64)
 // ---------------------------------------------------------------------------
+// out: this tile's slot in observable-major partials (observable j at
+// out[j * stride]).
 template <int NT>
-__device__ void block_reduce_obs(double v[kObs], double* __restrict__ out) {
+__device__ void block_reduce_obs(double v[kObs], double* __restrict__ out, int stride) {
     __shared__ double red[NT / 32][kObs];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -276,7 +278,7 @@ __device__ void block_reduce_obs(double v[kObs], double* __restrict__ out) {
         const int j = threadIdx.x;
         double acc = red[0][j];
         for (int w = 1; w < NT / 32; ++w) acc = (j == 9) ? fmax(acc, red[w][j]) : acc + red[w][j];
-        out[j] = acc;
+        out[(long long)j * stride] = acc;
     }
 }
 
@@ -733,7 +735,7 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
         double v[kObs];
 #pragma unroll
         for (int j = 0; j < kObs; ++j) v[j] = ob.total(j);
-        block_reduce_obs<NT>(v, partials + (long long)T.part * kObs);
+        block_reduce_obs<NT>(v, partials + T.part, I.part_stride);
     }
 }
 
@@ -1256,7 +1258,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                 const double u = __shfl_xor_sync(0xffffffffu, v, o);
                 v = (j == 9) ? fmax(v, u) : v + u;
             }
-            if (lane == 0) partials[(long long)W.part * kObs + j] = v;
+            if (lane == 0) partials[(long long)j * I.part_stride + W.part] = v;
         }
     }
 }
@@ -1487,10 +1489,11 @@ __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
 
 // Per-lattice reduction of the per-tile (or per-strip) partials: thread t
 // sums partials t, t + 256, ... in order, then a fixed shared-memory tree
-// combines the 256 sums, so the result does not depend on scheduling.
+// combines the 256 sums, so the result does not depend on scheduling. The
+// partials are observable-major, so each observable's loads are coalesced.
 constexpr int kRedThreads = 256;
 __device__ __forceinline__ void reduce_range(int begin, int end,
-                                             const double* __restrict__ partials,
+                                             const double* __restrict__ partials, int stride,
                                              double* __restrict__ out) {
     __shared__ double red[kObs][kRedThreads];
     const int t = threadIdx.x;
@@ -1500,7 +1503,7 @@ __device__ __forceinline__ void reduce_range(int begin, int end,
     for (int p = begin + t; p < end; p += kRedThreads) {
 #pragma unroll
         for (int j = 0; j < kObs; ++j) {
-            const double v = partials[(long long)p * kObs + j];
+            const double v = partials[(long long)j * stride + p];
             acc[j] = (j == 9) ? fmax(acc[j], v) : acc[j] + v;
         }
     }
@@ -1522,12 +1525,13 @@ __global__ void __launch_bounds__(kRedThreads)
 reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
            double* __restrict__ out) {
     const Inst& I = insts[blockIdx.x];
-    reduce_range(I.part_begin, I.part_end, partials, out + (long long)blockIdx.x * kObs);
+    reduce_range(I.part_begin, I.part_end, partials, I.part_stride,
+                 out + (long long)blockIdx.x * kObs);
 }
 
 __global__ void __launch_bounds__(kRedThreads)
 reduce_noalloc(int n_parts, const double* __restrict__ partials, double* __restrict__ out) {
-    reduce_range(0, n_parts, partials, out);
+    reduce_range(0, n_parts, partials, n_parts, out);
 }
 
 template <int TX, int TY>

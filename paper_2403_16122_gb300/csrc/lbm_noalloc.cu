@@ -63,6 +63,7 @@ extern "C" int lbm_step_noalloc(const lbm_params* p, const float* pops_in, const
     I.aux[1] = aux_out;
     I.part_begin = 0;
     I.part_end = (int)n_tiles;
+    I.part_stride = (int)n_tiles;
     cudaError_t e = lbmk::launch_step_noalloc(I, tiles_x, (int)n_tiles, scratch, d_obs,
                                               static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;

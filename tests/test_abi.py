@@ -86,3 +86,16 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_step_count(None) == -1
     lib.lbm_destroy(None)
+
+
+def test_largest_lattice_accepted_and_one_row_more_refused(lib):
+    """The state offsets are 32-bit: a lattice is accepted while 27 planes of
+    it stay below 2^31 elements (8192 x 9709 is the last 8192-wide one; its
+    two FP32 state buffers take 81 GB) and refused one row later."""
+    ok = inputs.params(nx=8192, ny=9709, periodic_x=1, periodic_y=0)
+    nbytes = lbm.lbm_workspace_size([ok])
+    assert nbytes >= 2 * 8192 * 9709 * 32 * 4
+    bad = inputs.params(nx=8192, ny=9710, periodic_x=1, periodic_y=0)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_workspace_size([bad])
+    assert e.value.code == lbm.LBM_EINVAL
