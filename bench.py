@@ -44,7 +44,7 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=1024, help="lattice size of the bubble drop")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--tune-steps", type=int, default=10)
+    ap.add_argument("--tune-steps", type=int, default=20)
     ap.add_argument("--kernel", default=None,
                     help="fixed layout 'kind,a,b,c' as lbm_set_kernel takes it (skips the autotuner)")
     ap.add_argument("--storage", choices=("fp32", "fp16"), default="fp32",

@@ -225,9 +225,9 @@ int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c)
 /* Current layout: out[0] = kind, out[1..3] = a, b, c as for lbm_set_kernel. */
 int lbm_get_kernel(const lbm_handle* h, int32_t* out);
 
-/* Autotuner: time every supported layout for this handle over `steps` time
-   steps each (after one warm-up step), measured with CUDA events on the
-   stream, and keep the fastest. The lattices are advanced by every step it
+/* Autotuner: time every supported layout for this handle twice over `steps`
+   time steps each (after one warm-up step), measured with CUDA events on the
+   stream, and keep the one with the shortest time. The lattices are advanced by every step it
    runs (lbm_step_count grows accordingly); all layouts compute identical
    results, so the trajectory is the one lbm_step would have produced.
    times_ms (may be NULL) receives up to `cap` mean step times in the order
