@@ -41,7 +41,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--n", type=int, default=1024, help="lattice size of the bubble drop")
+    ap.add_argument("--size", dest="n", type=int, default=1024, help="lattice size of the bubble drop")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-steps", type=int, default=20)
