@@ -68,7 +68,10 @@ extern "C" {
                    176 bytes per lattice update. Needs every lattice periodic
                    in x (strip layout). lbm_get_state / lbm_set_state convert
                    to and from the same double layouts as FP32.
-   LBM_STORE_BF16: reserved (LBM_EINVAL). */
+   LBM_STORE_BF16: the FP16 arrangement with bfloat16 values (7-bit
+                   mantissa, FP32 exponent range): 176 bytes per lattice
+                   update; the row-staged strip layout with 4 warps per CTA
+                   only (registers 128 or 168). */
 #define LBM_STORE_FP32  0
 #define LBM_STORE_FP16  1
 #define LBM_STORE_BF16  2

@@ -367,11 +367,12 @@ extern "C" {
 
 int lbm_workspace_size(const lbm_params* p, int32_t n_inst, int32_t storage, uint64_t* bytes) {
     if (!p || !bytes || n_inst < 1) return LBM_EINVAL;
-    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return LBM_EINVAL;
+    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16 && storage != LBM_STORE_BF16)
+        return LBM_EINVAL;
     for (int k = 0; k < n_inst; ++k) {
         if (!valid_params(p[k])) return LBM_EINVAL;
         // 16-bit storage runs in the strip layout, which needs periodic x
-        if (storage == LBM_STORE_FP16 && !p[k].periodic_x) return LBM_EINVAL;
+        if (storage != LBM_STORE_FP32 && !p[k].periodic_x) return LBM_EINVAL;
     }
     *bytes = make_layout(p, n_inst, storage).total;
     return LBM_OK;
@@ -546,7 +547,7 @@ int download_planar(lbm_handle* h, int32_t inst, std::vector<T>& tp, std::vector
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const int plane = (int)I.plane;
-    const bool half = h->storage == LBM_STORE_FP16;
+    const bool half = h->storage != LBM_STORE_FP32;
     std::vector<T> rp((size_t)lbmk::kPopElems * plane);
     std::vector<float> ra((size_t)aux_planes(h->storage) * plane);
     cudaError_t e = cudaMemcpyAsync(rp.data(), I.pop[h->parity], rp.size() * sizeof(T),
@@ -578,7 +579,7 @@ int upload_planar(lbm_handle* h, int32_t inst, const std::vector<T>& tp, const s
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const int plane = (int)I.plane;
-    const bool half = h->storage == LBM_STORE_FP16;
+    const bool half = h->storage != LBM_STORE_FP32;
     std::vector<T> rp((size_t)lbmk::kPopElems * plane, T());
     std::vector<float> ra((size_t)aux_planes(h->storage) * plane, 0.f);
     const size_t n = (size_t)p.nx * p.ny;
@@ -601,15 +602,16 @@ int upload_planar(lbm_handle* h, int32_t inst, const std::vector<T>& tp, const s
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host arrays die on return
     return e == cudaSuccess ? LBM_OK : cuda_fail(e);
 }
-}  // extern "C++"
 
-// FP16 storage: download, then decode every population with the references of
-// the site it streams into (the same arithmetic as the kernels' decode).
-int get_state_fp16(lbm_handle* h, int32_t inst, double* pops, double* aux) {
+// 16-bit storage (FP16 or BF16): download, then decode every population with
+// the references of the site it streams into (the kernels' decode).
+template <typename ST>
+int get_state_16(lbm_handle* h, int32_t inst, double* pops, double* aux) {
+    using C16 = lbmk::Bits16<ST>;
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
-    std::vector<__half> tp;
+    std::vector<ST> tp;
     std::vector<float> ta;
     const int rc = download_planar(h, inst, tp, ta);
     if (rc != LBM_OK) return rc;
@@ -625,9 +627,9 @@ int get_state_fp16(lbm_handle* h, int32_t inst, double* pops, double* aux) {
                 pops[18 * n + k] = ta[9 * n + k];                           // f_0
                 for (int i = 1; i < 9; ++i) {
                     const size_t kd = dest_site(p, x, y, i);
-                    const float rg = __half2float(tp[i * n + k]);
-                    const float rh = __half2float(tp[(9 + i) * n + k]);
-                    const float rf = __half2float(tp[(18 + i) * n + k]);
+                    const float rg = C16::to_f(tp[i * n + k]);
+                    const float rh = C16::to_f(tp[(9 + i) * n + k]);
+                    const float rf = C16::to_f(tp[(18 + i) * n + k]);
                     pops[i * n + k] = rg + kWf[i] * phr[kd];
                     pops[(9 + i) * n + k] = rh + kWf[i] * I.Cpref * Tr[kd];
                     pops[(18 + i) * n + k] = rf * (1.f / 4096.f) + kWf[i] * 3.f * ta[3 * n + k];
@@ -639,9 +641,11 @@ int get_state_fp16(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     return LBM_OK;
 }
 
-// FP16 storage: choose the references of every site from the given state
+// 16-bit storage: choose the references of every site from the given state
 // (phi_ref = sum g, T_ref from Eq. 9 on sum h), then encode.
-int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
+template <typename ST>
+int set_state_16(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
+    using C16 = lbmk::Bits16<ST>;
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
@@ -666,7 +670,7 @@ int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double
                           (1.0 - fs) * (ph * p.Cp + (1.0 - ph) * p.Cp * p.Cp_ratio_gl);
         Tr[k] = (float)(p.T_m + (H - Hs - L * fl) / cp);
     }
-    std::vector<__half> tp((size_t)27 * n);
+    std::vector<ST> tp((size_t)27 * n, C16::from_f(0.f));
     for (int y = 0; y < p.ny; ++y)
         for (int x = 0; x < p.nx; ++x) {
             const size_t k = (size_t)y * p.nx + x;
@@ -675,11 +679,11 @@ int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double
             ta[9 * n + k] = (float)pops[18 * n + k];
             for (int i = 1; i < 9; ++i) {
                 const size_t kd = dest_site(p, x, y, i);
-                tp[i * n + k] = __double2half(pops[i * n + k] - (double)(kWf[i] * phr[kd]));
+                tp[i * n + k] = C16::from_d(pops[i * n + k] - (double)(kWf[i] * phr[kd]));
                 tp[(9 + i) * n + k] =
-                    __double2half(pops[(9 + i) * n + k] - (double)(kWf[i] * I.Cpref * Tr[kd]));
+                    C16::from_d(pops[(9 + i) * n + k] - (double)(kWf[i] * I.Cpref * Tr[kd]));
                 const double fr = (double)(kWf[i] * 3.f * ta[3 * n + k]);
-                tp[(18 + i) * n + k] = __double2half((pops[(18 + i) * n + k] - fr) * 4096.0);
+                tp[(18 + i) * n + k] = C16::from_d((pops[(18 + i) * n + k] - fr) * 4096.0);
             }
         }
     const int rc = upload_planar(h, inst, tp, ta);
@@ -688,13 +692,15 @@ int set_state_fp16(lbm_handle* h, int32_t inst, const double* pops, const double
     h->have_obs = false;
     return LBM_OK;
 }
+}  // extern "C++"
 
 }  // namespace
 
 int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     if (!inst_ok(h, inst)) return LBM_EINVAL;
     if (!h->initialised) return LBM_ESTATE;
-    if (h->storage == LBM_STORE_FP16) return get_state_fp16(h, inst, pops, aux);
+    if (h->storage == LBM_STORE_FP16) return get_state_16<__half>(h, inst, pops, aux);
+    if (h->storage == LBM_STORE_BF16) return get_state_16<__nv_bfloat16>(h, inst, pops, aux);
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
@@ -713,7 +719,8 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
 
 int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
     if (!inst_ok(h, inst) || !pops || !aux) return LBM_EINVAL;
-    if (h->storage == LBM_STORE_FP16) return set_state_fp16(h, inst, pops, aux);
+    if (h->storage == LBM_STORE_FP16) return set_state_16<__half>(h, inst, pops, aux);
+    if (h->storage == LBM_STORE_BF16) return set_state_16<__nv_bfloat16>(h, inst, pops, aux);
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
@@ -759,6 +766,7 @@ int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c)
             if (!h->params[k].periodic_x) return LBM_EINVAL;
         if (!lbmk::strip_supported(a, c) || (b != 0 && b < kMinRows)) return LBM_EINVAL;
         if (kind == LBM_KERNEL_STAGED && !lbmk::staged_supported(a, c, h->storage)) return LBM_EINVAL;
+        if (kind == LBM_KERNEL_STRIP && h->storage == LBM_STORE_BF16) return LBM_EINVAL;  // staged only
         h->kind = kind; h->warps = a; h->rows_req = b; h->regs = c;
     } else {
         return LBM_EINVAL;

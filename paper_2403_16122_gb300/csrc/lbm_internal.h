@@ -2,6 +2,8 @@
 // kernel and host-API translation units of liblbmfreeze (not installed).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,6 +40,27 @@ enum : int {
 // h_0 is stored shifted by -L f_l of the same site and step, which keeps every
 // stored value O(1) (the latent part of H is carried by f_l instead).
 constexpr int kPopElems = 24;
+
+// The two 16-bit storage types (FP16: 10-bit mantissa, BF16: 7-bit mantissa
+// and the FP32 exponent range) behind one set of conversions.
+template <typename ST>
+struct Bits16;
+template <>
+struct Bits16<__half> {
+    static __host__ __device__ float to_f(__half v) { return __half2float(v); }
+    static __host__ __device__ __half from_f(float v) { return __float2half_rn(v); }
+    static __host__ __device__ __half from_d(double v) { return __double2half(v); }
+    static __host__ __device__ __half from_bits(unsigned short b) { return __ushort_as_half(b); }
+    static __host__ __device__ unsigned short bits(__half v) { return __half_as_ushort(v); }
+};
+template <>
+struct Bits16<__nv_bfloat16> {
+    static __host__ __device__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __host__ __device__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+    static __host__ __device__ __nv_bfloat16 from_d(double v) { return __double2bfloat16(v); }
+    static __host__ __device__ __nv_bfloat16 from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
+    static __host__ __device__ unsigned short bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+};
 __host__ __device__ inline int gh_at(int i, int plane, int site, int set) {
     return 2 * (i - 1) * plane + 2 * site + set;
 }

@@ -85,8 +85,8 @@ __device__ __forceinline__ float ld_f32(const float* p) {
     if constexpr (NC) return __ldg(p); else return __ldcg(p);
 }
 template <bool NC>
-__device__ __forceinline__ float ld_f16(const __half* p) {
-    if constexpr (NC) return __half2float(__ldg(p)); else return __half2float(__ldcg(p));
+__device__ __forceinline__ unsigned short ld_u16(const unsigned short* p) {
+    if constexpr (NC) return __ldg(p); else return __ldcg(p);
 }
 
 // FP16 storage: population i of a set is stored as a 16-bit deviation from a
@@ -118,8 +118,8 @@ __device__ __forceinline__ float ldPop(const LatT<NC>& l, int set, int i, int id
     if constexpr (sizeof(ST) == 4) {
         return ld_f32<NC>(l.A + pop_at(set, i, l.plane, idx));
     } else {
-        const __half* A = reinterpret_cast<const __half*>(l.A);
-        return ld_f16<NC>(A + pop_at(set, i, l.plane, idx));
+        const unsigned short* A = reinterpret_cast<const unsigned short*>(l.A);
+        return Bits16<ST>::to_f(Bits16<ST>::from_bits(ld_u16<NC>(A + pop_at(set, i, l.plane, idx))));
     }
 }
 
@@ -490,18 +490,18 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                 // deviations from the rest equilibria (g, h: destination's
                 // references dref[i]; f: this site's pressure), and what their
                 // rounding to 16 bits takes away from what the site sends
-                __half* B = static_cast<__half*>(Bv);
+                using C16 = Bits16<ST>;
+                unsigned short* B = static_cast<unsigned short*>(Bv);
                 const Ref& d = dref[i];
                 const float dg = gn - w * d.phi, dh = hn - w * P.Cpref * d.T;
                 const float df = (fn - f_rest(i, pn)) * kFScale;
-                const __half qg = __float2half_rn(dg);
-                const __half qh = __float2half_rn(dh);
-                const __half qf = __float2half_rn(df);
-                *reinterpret_cast<__half2*>(B + gh_at(i, plane, own, 0)) = __halves2half2(qg, qh);
-                B[f_at(i, plane, own)] = qf;
-                eg += dg - __half2float(qg);
-                eh += dh - __half2float(qh);
-                ef += df - __half2float(qf);
+                const ST qg = C16::from_f(dg), qh = C16::from_f(dh), qf = C16::from_f(df);
+                *reinterpret_cast<unsigned*>(B + gh_at(i, plane, own, 0)) =
+                    (unsigned)C16::bits(qg) | ((unsigned)C16::bits(qh) << 16);
+                B[f_at(i, plane, own)] = C16::bits(qf);
+                eg += dg - C16::to_f(qg);
+                eh += dh - C16::to_f(qh);
+                ef += df - C16::to_f(qf);
             }
         }
     }
@@ -894,7 +894,7 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, i
     cp_async16(slot + 4 * lane, l.Aaux + own0_at(own, 0));
     cp_async16(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(plane, own, 0));
     if constexpr (kHalf) cp_async8(slot + kSlotR + 2 * lane, l.Aaux + ref_at(plane, own, 0));
-    const __half* A16 = reinterpret_cast<const __half*>(l.A);
+    const unsigned short* A16 = reinterpret_cast<const unsigned short*>(l.A);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int cy = CY(i), cx = CX(i);
@@ -952,13 +952,14 @@ __device__ __forceinline__ void staged_set(const float* slot, int lane, int r, i
         const bool wall = (CY(i) > 0 && wlo) || (CY(i) < 0 && whi);
         if (SET < 2) {
             const unsigned w = __float_as_uint(slot[slot_gh(i, lane)]);
-            const float raw =
-                __half2float(__ushort_as_half((unsigned short)(SET == 0 ? (w & 0xffffu) : (w >> 16))));
+            const float raw = Bits16<ST>::to_f(
+                Bits16<ST>::from_bits((unsigned short)(SET == 0 ? (w & 0xffffu) : (w >> 16))));
             v[i] = SET == 0 ? raw + WGT(i) * ref.phi : raw + WGT(i) * Cpref * ref.T;
         } else {
             const unsigned w = __float_as_uint(slot[slot_f(i, lane)]);
             const unsigned sel = wall ? par.c : (CX(i) > 0 ? par.m : (CX(i) < 0 ? par.p : par.c));
-            const float raw = __half2float(__ushort_as_half((unsigned short)__byte_perm(w, 0u, sel)));
+            const float raw =
+                Bits16<ST>::to_f(Bits16<ST>::from_bits((unsigned short)__byte_perm(w, 0u, sel)));
             v[i] = raw * kInvFScale + f_rest(i, wall ? pref[0] : pref[i]);
         }
         if (SET == 1 && wall) {
@@ -1438,7 +1439,8 @@ __device__ __forceinline__ double init_T(const InitConst& c, double phi, double 
     return init_site(c, phi, T0).T;
 }
 
-__global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
+template <typename ST>
+__global__ void init_16(const Inst* __restrict__ insts, int inst, InitConst c,
                           const double* __restrict__ phi0, const double* __restrict__ T0,
                           int parity) {
     const Inst& I = insts[inst];
@@ -1450,7 +1452,7 @@ __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
         const double ph = phi0[k];
         const InitSite st = init_site(c, ph, T0[k]);
         const double H = st.H, fl = st.fl, T = st.T;
-        __half* P = static_cast<__half*>(I.pop[parity]);
+        ST* P = static_cast<ST*>(I.pop[parity]);
         float* A = I.aux[parity];
         const float phr = (float)ph, Tr = (float)T;
         for (int i = 0; i < 9; ++i) {
@@ -1475,10 +1477,10 @@ __global__ void init_fp16(const Inst* __restrict__ insts, int inst, InitConst c,
                 A[own0_at(idx, 2)] = 0.f;
                 continue;
             }
-            P[gh_at(i, plane, idx, 0)] = __double2half(w * ph - (double)(wf * phd));  // Eq. 24, u = 0
+            P[gh_at(i, plane, idx, 0)] = Bits16<ST>::from_d(w * ph - (double)(wf * phd));  // Eq. 24, u = 0
             P[gh_at(i, plane, idx, 1)] =
-                __double2half(w * c.Cp * T * (c.Cpref / c.Cp) - (double)(wf * I.Cpref * Td));  // Eq. 28
-            P[f_at(i, plane, idx)] = __float2half_rn(0.f);  // Eq. 31 vanishes at p = 0, u = 0
+                Bits16<ST>::from_d(w * c.Cp * T * (c.Cpref / c.Cp) - (double)(wf * I.Cpref * Td));  // Eq. 28
+            P[f_at(i, plane, idx)] = Bits16<ST>::from_f(0.f);  // Eq. 31 vanishes at p = 0, u = 0
         }
         A[own0_at(idx, 3)] = (float)fl;
         for (int k = 0; k < 4; ++k) A[own1_at(plane, idx, k)] = 0.f;
@@ -1703,14 +1705,28 @@ cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_in
     return launch_strip_st<float>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials, s);
 }
 
+// BF16 storage is built for the two four-warp staged variants only.
+using bf16 = __nv_bfloat16;
+template <typename F>
+auto staged_dispatch_bf16(int regs, F&& f) -> decltype(f(Staged<4, 3, 4, bf16>())) {
+    if (regs == 128) return f(Staged<4, 4, 3, bf16>());
+    return f(Staged<4, 3, 4, bf16>());
+}
+template <typename F>
+auto storage_dispatch(int storage, int warps, int regs, F&& f) -> decltype(f(Staged<4, 3, 4, float>())) {
+    if (storage == LBM_STORE_FP16) return staged_dispatch<__half>(warps, regs, f);
+    if (storage == LBM_STORE_BF16) return staged_dispatch_bf16(regs, f);
+    return staged_dispatch<float>(warps, regs, f);
+}
+
 bool staged_supported(int warps, int regs, int storage) {
+    if (storage == LBM_STORE_BF16) return warps == 4 && (regs == 128 || regs == 168);
     return (storage == LBM_STORE_FP32 || storage == LBM_STORE_FP16) && strip_supported(warps, regs);
 }
 
 cudaError_t prepare_staged(int warps, int regs, int storage) {
     auto go = [](auto v) { return decltype(v)::prepare(); };
-    return storage == LBM_STORE_FP16 ? staged_dispatch<__half>(warps, regs, go)
-                                     : staged_dispatch<float>(warps, regs, go);
+    return storage_dispatch(storage, warps, regs, go);
 }
 
 cudaError_t launch_step_staged(int warps, int regs, int storage, const Inst* d_inst,
@@ -1721,17 +1737,17 @@ cudaError_t launch_step_staged(int warps, int regs, int storage, const Inst* d_i
     auto go = [&](auto v) {
         return decltype(v)::launch(d_inst, d_items, n_items, parity, obs, d_partials, s);
     };
-    return storage == LBM_STORE_FP16 ? staged_dispatch<__half>(warps, regs, go)
-                                     : staged_dispatch<float>(warps, regs, go);
+    return storage_dispatch(storage, warps, regs, go);
 }
 
 int strip_resident_warps(int staged, int warps, int regs, int storage) {
     if (!strip_supported(warps, regs)) return 0;
     if (staged) {
+        if (!staged_supported(warps, regs, storage)) return 0;
         auto go = [](auto v) { return decltype(v)::resident_warps(); };
-        return storage == LBM_STORE_FP16 ? staged_dispatch<__half>(warps, regs, go)
-                                         : staged_dispatch<float>(warps, regs, go);
+        return storage_dispatch(storage, warps, regs, go);
     }
+    if (storage == LBM_STORE_BF16) return 0;  // plain strips: FP32 and FP16
     auto pick = [&](auto tag) -> int {
         using ST = decltype(tag);
         if (warps == 4 && regs == 128) return plain_resident_warps<4, 4, ST>();
@@ -1746,6 +1762,10 @@ int strip_resident_warps(int staged, int warps, int regs, int storage) {
 int persistent_grid(int staged, int warps, int regs, int storage, int n_items) {
     if (!strip_supported(warps, regs) || n_items <= 0) return 0;
     auto g = [&](auto v) { return decltype(v)::grid(n_items); };
+    if (storage == LBM_STORE_BF16) {
+        if (!staged || !staged_supported(warps, regs, storage)) return 0;
+        return regs == 128 ? g(Persist<4, 4, 3, bf16>()) : g(Persist<4, 3, 4, bf16>());
+    }
     if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(staged, warps, regs, g);
     return persist_dispatch<float>(staged, warps, regs, g);
 }
@@ -1760,6 +1780,10 @@ cudaError_t launch_step_strip_persistent(int staged, int warps, int regs, int st
         return decltype(v)::launch(grid, d_inst, d_items, n_items, parity0, nsteps, d_bar, d_err,
                                    limit_ns, s);
     };
+    if (storage == LBM_STORE_BF16) {
+        if (!staged || !staged_supported(warps, regs, storage)) return cudaErrorInvalidValue;
+        return regs == 128 ? go(Persist<4, 4, 3, bf16>()) : go(Persist<4, 3, 4, bf16>());
+    }
     if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(staged, warps, regs, go);
     if (storage != LBM_STORE_FP32) return cudaErrorNotSupported;
     return persist_dispatch<float>(staged, warps, regs, go);
@@ -1815,7 +1839,9 @@ cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage, 
     if (storage == LBM_STORE_FP32)
         init_fp32<<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
     else if (storage == LBM_STORE_FP16)
-        init_fp16<<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
+        init_16<__half><<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
+    else if (storage == LBM_STORE_BF16)
+        init_16<__nv_bfloat16><<<blocks, threads, 0, s>>>(d_inst, inst, c, d_phi0, d_T0, parity);
     else
         return cudaErrorNotSupported;
     return cudaGetLastError();

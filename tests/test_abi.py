@@ -71,9 +71,13 @@ def test_invalid_parameters_rejected(lib, bad):
 
 def test_unsupported_storage_rejected(lib):
     p = inputs.params()
-    for st in (7, lbm.LBM_STORE_BF16):
-        with pytest.raises(lbm.LbmError):
-            lbm.lbm_workspace_size([p], storage=st)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_size([p], storage=7)
+    # BF16 takes the FP16 arrangement, and like it needs the strip layouts
+    assert lbm.lbm_workspace_size([p], storage=lbm.LBM_STORE_BF16) == \
+        lbm.lbm_workspace_size([p], storage=lbm.LBM_STORE_FP16)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_workspace_size([dict(p, periodic_x=0)], storage=lbm.LBM_STORE_BF16)
 
 
 def test_error_strings(lib):
