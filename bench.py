@@ -392,6 +392,22 @@ def run_ours(args, dist: Dist):
         }
         lat16.close()
 
+    # BF16 storage (same arrangement, bfloat16 values) on the same lattice
+    if forms is not None:
+        latb = lbm.Lattice([p], storage=lbm.LBM_STORE_BF16, device=dev)
+        latb.init(phi0, T0)
+        latb.step(max(args.warmup, 3))
+        if not args.no_autotune:
+            latb.autotune(steps=args.tune_steps)
+        kb = max(1, min(args.steps, 3000))
+        msb = _timed_steps(latb, kb)
+        forms["bf16_storage"] = {
+            "value": sites / (msb * 1e-3) / 1e6, "unit": "MLUPS", "steps": kb, "ms_per_step": msb,
+            "bytes_per_lu": BYTES_PER_LU_FP16,
+            "hbm_frac": BYTES_PER_LU_FP16 * sites / (msb * 1e-3) / 1e9 / peak,
+            "speedup_vs_fp32": ms_per_step / msb, "kernel": list(latb.kernel)}
+        latb.close()
+
     # the Boussinesq option (Section 4.3) on the same lattice: one more force
     # term per site
     if forms is not None:
