@@ -20,7 +20,6 @@ using lbmk::Tile;
 
 namespace {
 
-constexpr int kTileMinSites = 32 * 4;  // smallest supported tile (sizes the partials)
 constexpr uint64_t kAlign = 256;
 constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // device-wide barrier wait
 constexpr int kMaxChunk = 1 << 16;
@@ -132,7 +131,6 @@ Layout make_layout(const lbm_params* p, int n, int storage) {
         }
     }
     L.total = off;
-    (void)kTileMinSites;
     return L;
 }
 

@@ -125,13 +125,13 @@ __device__ __forceinline__ float ldPop(const LatT<NC>& l, int set, int i, int id
 
 // Stored value -> population (h_0 in the shifted form) for site reference r.
 template <typename ST, int SET>
-__device__ __forceinline__ float decode(int i, float raw, const Ref& r, float Cpref, float h0ref) {
+__device__ __forceinline__ float decode(int i, float raw, const Ref& r, float Cpref) {
     if constexpr (sizeof(ST) == 4) {
         return raw;
     } else {
         if (i == 0) return raw;  // rest populations are stored in FP32
         if (SET == 0) return raw + WGT(i) * r.phi;
-        if (SET == 1) return i == 0 ? raw + r.T * h0ref : raw + WGT(i) * Cpref * r.T;
+        if (SET == 1) return raw + WGT(i) * Cpref * r.T;
         return raw * kInvFScale;  // the caller adds the source-pressure reference
     }
 }
@@ -153,10 +153,10 @@ __device__ __forceinline__ float ldAux(const LatT<NC>& l, int k, int idx) {
 template <int SET, typename ST = float, bool NC>
 __device__ __forceinline__ void pull_set(const LatT<NC>& l, int x, int y, float abb, float v[9],
                                          const Ref& ref = Ref{0.f, 0.f}, float Cpref = 0.f,
-                                         float h0ref = 0.f, const float* pref = nullptr) {
+                                         const float* pref = nullptr) {
     constexpr bool kFref = sizeof(ST) != 4 && SET == 2;  // f: source-pressure reference
     const int own = y * l.pitch + x;
-    v[0] = decode<ST, SET>(0, ldPop<ST>(l, SET, 0, own), ref, Cpref, h0ref);
+    v[0] = decode<ST, SET>(0, ldPop<ST>(l, SET, 0, own), ref, Cpref);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int xs = x - CX(i), ys = y - CY(i);
@@ -176,10 +176,10 @@ __device__ __forceinline__ void pull_set(const LatT<NC>& l, int x, int y, float 
             else { wall = true; dir |= (l.flags & kDirYhi) != 0; }
         }
         if (!wall) {
-            v[i] = decode<ST, SET>(i, ldPop<ST>(l, SET, i, ys * l.pitch + xs), ref, Cpref, h0ref);
+            v[i] = decode<ST, SET>(i, ldPop<ST>(l, SET, i, ys * l.pitch + xs), ref, Cpref);
             if constexpr (kFref) v[i] += f_rest(i, pref[i]);
         } else {
-            float b = decode<ST, SET>(OPP(i), ldPop<ST>(l, SET, OPP(i), own), ref, Cpref, h0ref);
+            float b = decode<ST, SET>(OPP(i), ldPop<ST>(l, SET, OPP(i), own), ref, Cpref);
             if constexpr (kFref) b += f_rest(OPP(i), pref[0]);  // bounced: the site itself
             if (SET == 1 && dir) b = -b + 2.0f * WGT(i) * abb;
             v[i] = b;
@@ -191,7 +191,6 @@ struct Phys {
     float L, Hs, Tm, Cp, Cpref, Tw, omega_g, omega_h, kappa, beta, lam_coef;
     float rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, mdot_coef, tan_w, inv_ramp, eps2;
     float inv_L, inv_Cp;
-    float h0ref;   // Cp - (1 - w0) Cp_ref: T-coefficient of the rest h_0 (shifted)
     float buoy_x, buoy_y, T_ref;
     float Cp_s, Cp_g, k_s, k_g, dtau_h;
     bool phase_props;
@@ -205,7 +204,6 @@ __device__ __forceinline__ Phys load_phys(const Inst& I) {
     P.mu_s = I.mu_s; P.mu_l = I.mu_l; P.mu_g = I.mu_g; P.mdot_coef = I.mdot_coef;
     P.tan_w = I.tan_w; P.inv_ramp = I.inv_ramp; P.eps2 = I.normal_eps2;
     P.inv_L = I.inv_L; P.inv_Cp = I.inv_Cp;
-    P.h0ref = I.Cp - (1.f - kW0) * I.Cpref;
     P.buoy_x = I.buoy_x; P.buoy_y = I.buoy_y; P.T_ref = I.T_ref;
     P.Cp_s = I.Cp_s; P.Cp_g = I.Cp_g; P.k_s = I.k_s; P.k_g = I.k_g; P.dtau_h = I.dtau_h;
     P.phase_props = (I.flags & kPhaseProps) != 0;
@@ -780,12 +778,12 @@ step_tile_noalloc(const Inst I, int tiles_x, double* __restrict__ partials) {
 template <int SET, typename ST, bool NC>
 __device__ __forceinline__ void pull_rows(const LatT<NC>& l, int xc, int xm, int xp, int r0,
                                           int rm, int rp, float v[9], const Ref& ref,
-                                          float Cpref, float h0ref, const float* pref) {
+                                          float Cpref, const float* pref) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int r = CY(i) > 0 ? rm : (CY(i) < 0 ? rp : r0);   // source row y - cy
         const int c = CX(i) > 0 ? xm : (CX(i) < 0 ? xp : xc);   // source column x - cx
-        v[i] = decode<ST, SET>(i, ldPop<ST>(l, SET, i, r + c), ref, Cpref, h0ref);
+        v[i] = decode<ST, SET>(i, ldPop<ST>(l, SET, i, r + c), ref, Cpref);
         if constexpr (sizeof(ST) != 4 && SET == 2) {
             if (i) v[i] += f_rest(i, pref[i]);
         }
@@ -801,15 +799,15 @@ struct RowCtx {
 template <int SET, typename ST = float, bool NC>
 __device__ __forceinline__ void pull_row(const LatT<NC>& l, const RowCtx& c, int y, float abb,
                                          float v[9], const Ref& ref = Ref{0.f, 0.f},
-                                         float Cpref = 0.f, float h0ref = 0.f,
+                                         float Cpref = 0.f,
                                          const float* pref = nullptr) {
     if (c.py || (y >= 1 && y <= l.ny - 2)) {
         const int ym = y == 0 ? l.ny - 1 : y - 1;
         const int yp = y == l.ny - 1 ? 0 : y + 1;
         pull_rows<SET, ST>(l, c.xc, c.xm, c.xp, y * l.pitch, ym * l.pitch, yp * l.pitch, v, ref,
-                           Cpref, h0ref, pref);
+                           Cpref, pref);
     } else {
-        pull_set<SET, ST>(l, c.xc, y, abb, v, ref, Cpref, h0ref, pref);
+        pull_set<SET, ST>(l, c.xc, y, abb, v, ref, Cpref, pref);
     }
 }
 
@@ -1018,8 +1016,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         float gg[9], hh[9];
         const int idx = y * l.pitch + x_outer;
         const Ref r = site_ref(idx);
-        pull_set<0, ST>(l, x_outer, y, abb, gg, r, P.Cpref, P.h0ref);
-        pull_set<1, ST>(l, x_outer, y, abb, hh, r, P.Cpref, P.h0ref);
+        pull_set<0, ST>(l, x_outer, y, abb, gg, r, P.Cpref);
+        pull_set<1, ST>(l, x_outer, y, abb, hh, r, P.Cpref);
         return local_macro(P, gg, hh, ldAux(l, 0, idx)).phi;
     };
     auto note_outer = [&](int y) {
@@ -1035,8 +1033,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         float gg[9], hh[9];
         const int idx = y * l.pitch + c.xc;
         r = site_ref(idx);
-        pull_row<0, ST>(l, c, y, abb, gg, r, P.Cpref, P.h0ref);
-        pull_row<1, ST>(l, c, y, abb, hh, r, P.Cpref, P.h0ref);
+        pull_row<0, ST>(l, c, y, abb, gg, r, P.Cpref);
+        pull_row<1, ST>(l, c, y, abb, hh, r, P.Cpref);
         m = local_macro(P, gg, hh, ldAux(l, 0, idx));
         p = ldAux(l, 3, idx);
         S = ldAux(l, 4, idx);
@@ -1138,7 +1136,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                 staged_set<2, ST>(slot(jy), lane, y, ny, c.py, l.flags, abb, f, par, rO, P.Cpref,
                                   pref);
             else
-                pull_row<2, ST>(l, c, y, abb, f, rO, P.Cpref, P.h0ref, pref);
+                pull_row<2, ST>(l, c, y, abb, f, rO, P.Cpref, pref);
         };
         float phiux_p, phiuy_p;
         if constexpr (STG > 0) {
@@ -1234,8 +1232,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                 staged_set<0, ST>(slot(jy), lane, y, ny, c.py, l.flags, abb, g, par, rO, P.Cpref);
                 staged_set<1, ST>(slot(jy), lane, y, ny, c.py, l.flags, abb, h, par, rO, P.Cpref);
             } else {
-                pull_row<0, ST>(l, c, y, abb, g, rO, P.Cpref, P.h0ref);
-                pull_row<1, ST>(l, c, y, abb, h, rO, P.Cpref, P.h0ref);
+                pull_row<0, ST>(l, c, y, abb, g, rO, P.Cpref);
+                pull_row<1, ST>(l, c, y, abb, h, rO, P.Cpref);
             }
             site_update<OBS, ST>(P, l.flags, mO, ArrPops{g, h, f}, phiux_p, phiuy_p, st, B, Baux,
                                  l.plane, own, c.xc == nx / 2, y == ny / 2, ob, dref);
