@@ -347,7 +347,11 @@ def run_ours(args, dist: Dist):
         ph.numpy()[:] = phi0
         tt.numpy()[:] = T0
         lat2 = lbm.Lattice([p], device=dev)
-        lat2.set_kernel(*kernel)
+        # tuned, as a caller reading the observables after every step would,
+        # on single observable steps; then back to the initial state
+        lat2.init(ph.numpy(), tt.numpy())
+        lat2.autotune(steps=1)
+        kernel_e2e = lat2.kernel
         torch.cuda.synchronize()
         dist.barrier()
         t0 = time.perf_counter()
@@ -359,8 +363,10 @@ def run_ours(args, dist: Dist):
         ev, _ = aggregate(sites * k_e2e, dt * 1e3, dist)
         e2e = {"value": ev, "unit": "MLUPS", "h2d_bytes_per_step": 16 * sites / k_e2e,
                "d2h_bytes_per_step": 8 * lbm.LBM_OBS_COUNT, "steps": k_e2e,
+               "kernel": list(kernel_e2e),
                "what": "lbm_init_fields from pinned host phi0/T0, then per step lbm_step(1) + "
-                       "lbm_observables (device-to-host read, synchronising)"}
+                       "lbm_observables (device-to-host read, synchronising); the kernel "
+                       "tuned by lbm_autotune on single observable steps, before the timed region"}
         lat2.close()
 
     # the FP16-storage form on the same workload and GPU (FP32 arithmetic)
@@ -565,6 +571,20 @@ def batched_forms(args, dev, peak):
         res[name] = (ms, lat.exec, lat.kernel, lat.observables_all(check=False))
         lat.close()
     ms32, ms16 = res["fp32"][0], res["fp16"][0]
+    # each lattice's own step time when run by itself, on a seeded sample of
+    # the batch (every one of the 1024 would take most of a minute)
+    pick = np.random.default_rng(20240324).choice(len(mixed), size=min(64, len(mixed)),
+                                                  replace=False)
+    alone = {}
+    for name, st in (("fp32", lbm.LBM_STORE_FP32), ("fp16", lbm.LBM_STORE_FP16)):
+        per = []
+        for i in sorted(pick.tolist()):
+            c = mixed[i]
+            h = lbm.Lattice([c[0]], storage=st, device=dev)
+            h.init(c[1], c[2]).step(3)
+            per.append(_timed_steps(h, 8))
+            h.close()
+        alone[name] = np.array(per)
     i_s, i_v = lbm.OBS_NAMES.index("solid"), lbm.OBS_NAMES.index("volume")
     o32, o16 = res["fp32"][3], res["fp16"][3]
     out["batched_fp16_bubbles1024"] = {
@@ -577,6 +597,12 @@ def batched_forms(args, dev, peak):
         "speedup_vs_fp32_batched": ms32 / ms16,
         "exec": {"mode": "persistent+graph", "chunk": res["fp16"][1][1], "ctas": res["fp16"][1][2]},
         "kernel": list(res["fp16"][2]),
+        "instance_ms_per_step": {
+            "batched_all": ms16, "batched_all_fp32": ms32, "alone_sample": int(len(pick)),
+            "alone_p50": float(np.percentile(alone["fp16"], 50)),
+            "alone_p99": float(np.percentile(alone["fp16"], 99)),
+            "alone_fp32_p50": float(np.percentile(alone["fp32"], 50)),
+            "alone_fp32_p99": float(np.percentile(alone["fp32"], 99))},
         "max_rel_diff_vs_fp32": {
             "volume": float(np.max(np.abs(o16[:, i_v] - o32[:, i_v]) / np.abs(o32[:, i_v]))),
             "solid": float(np.max(np.abs(o16[:, i_s] - o32[:, i_s]) / np.maximum(o32[:, i_s], 1.0))),
