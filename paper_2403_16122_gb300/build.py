@@ -9,6 +9,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import re
 import shutil
 import subprocess
 
@@ -52,12 +53,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
+        # the register and spill report of every kernel is kept beside the
+        # object (ptxas_report reads it)
+        cmd = [cc, *ARCH, *FLAGS, "-Xptxas=-v", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+        with open(obj + ".ptxas.txt", "w") as f:
+            f.write(r.stderr)
         return obj, r.stderr
 
     with cf.ThreadPoolExecutor(max_workers=max(1, len(sources()))) as ex:
@@ -71,6 +74,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def ptxas_report() -> dict:
+    """{mangled kernel name: (registers, spill store bytes)} from the report of
+    the last build."""
+    out = {}
+    for path in glob.glob(os.path.join(OUT_DIR, "*.o.ptxas.txt")):
+        cur, spill = None, 0
+        for line in open(path):
+            m = re.search(r"Compiling entry function '([^']+)'", line)
+            if m:
+                cur, spill = m.group(1), 0
+                continue
+            m = re.search(r"(\d+) bytes spill stores", line)
+            if m and cur:
+                spill = int(m.group(1))
+            m = re.search(r"Used (\d+) registers", line)
+            if m and cur:
+                out[cur] = (int(m.group(1)), spill)
+                cur = None
+    return out
 
 
 if __name__ == "__main__":
