@@ -5,11 +5,12 @@ Each case is chosen so that a plausible slip in the step (a dropped term, a
 wrong sign or index, a transposed operand, a wrong relaxation time) fails at
 least one of them."""
 import math
+import os
 
 import numpy as np
 import pytest
 from scipy.optimize import brentq
-from scipy.special import erf
+from scipy.special import erf, erfc
 
 from paper_2403_16122_gb300 import inputs
 
@@ -24,6 +25,27 @@ def neumann_lambda(ste: float) -> float:
 
 def run(oracle_mod, p, phi0, T0):
     return oracle_mod.Oracle(p).init(phi0, T0)
+
+
+def golden(name: str) -> dict:
+    """The key-value pairs of tests/golden/<name> (its comment lines cite the
+    passage the values come from)."""
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if len(line) == 2:
+                out[line[0]] = float(line[1])
+    return out
+
+
+def neumann_two_phase_lambda(ste: float, superheat: float) -> float:
+    """Root of exp(-l^2) (1 / erf(l) - superheat / erfc(l)) = l sqrt(pi) / Ste:
+    the two-phase Stefan problem with equal properties in both phases, the
+    liquid initially superheat (T0 - T_m) / (T_m - T_w) above the melting
+    point."""
+    return brentq(lambda l: math.exp(-l * l) * (1.0 / erf(l) - superheat / erfc(l))
+                  - l * math.sqrt(math.pi) / ste, 1e-6, 3.0)
 
 
 # ---------------------------------------------------------------------------
@@ -95,6 +117,49 @@ def test_stefan_front_follows_neumann(oracle_mod, ste, times):
         s = o.observables()["solid"] / p["ny"]
         s_exact = 2 * lam * math.sqrt(alpha * t)
         assert abs(s - s_exact) <= 1.0, (t, s, s_exact)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("which", ["Ste_min", "Ste_max"])
+def test_stefan_as_printed_follows_two_phase_neumann(oracle_mod, which):
+    """Section 4.1 with the temperatures it prints (tests/golden): liquid at
+    T0 = 0.1 above T_m = 0, wall at T_w = -2, W = 5, along 400 cells. With
+    rho_s = rho_l nothing flows and the two-phase Neumann solution holds: the
+    front at s = 2 lambda sqrt(alpha t), the solid at T_w + (T_m - T_w)
+    erf(xi) / erf(lambda), the liquid (and the gas beyond it, which conducts
+    alike) at T0 - (T0 - T_m) erfc(xi) / erfc(lambda), xi = d / (2 sqrt(alpha
+    t)) at distance d from the wall. The liquid profile carries the superheat
+    that the one-phase case above does not have. An enthalpy front that
+    crosses whole cells leaves a first-order error behind it: it falls as 1/s,
+    so it must halve (within 20 %) when the front has travelled twice as far
+    (t x 4), and stay below a fifth of the superheat and 2 % of T_m - T_w at
+    s = 25 cells. Liquid-side conduction missing or of the wrong strength
+    leaves an error of the order of the whole superheat that does not fall."""
+    g = golden("stefan_section4_1.txt")
+    ste, T0, Tw, Tm = g[which], g["T0"], g["T_w"], g["T_m"]
+    n = int(g["grid_long"])
+    # the short direction is periodic and the solution uniform across it
+    p, phi0, _ = inputs.stefan(nx=n, ny=4, H0=350, Ste=ste, rho_ratio_sl=1.0, W=g["W"],
+                               T_w=Tw, T_m=Tm)
+    o = run(oracle_mod, p, phi0, np.full(phi0.shape, T0))
+    lam = neumann_two_phase_lambda(ste, (T0 - Tm) / (Tm - Tw))
+    alpha = CS2 * (p["tau_h"] - 0.5)
+    d = np.arange(n) + 0.5  # distance of each cell from the wall at x = -1/2
+    err = []
+    for t in (8000, 32000):
+        o.step(t - o.step_count)
+        s = o.observables()["solid"] / p["ny"]
+        assert abs(s - 2 * lam * math.sqrt(alpha * t)) <= 1.0, (t, s)
+        T = o.fields()["T"].mean(axis=0)
+        xi = d / (2 * math.sqrt(alpha * t))
+        solid, liquid = d < s - 1.5, (d > s + 1.5) & (d < 300)
+        e_s = np.abs(T[solid] - (Tw + (Tm - Tw) * erf(xi[solid]) / erf(lam))).max()
+        e_l = np.abs(T[liquid] - (T0 - (T0 - Tm) * erfc(xi[liquid]) / erfc(lam))).max()
+        err.append((e_s, e_l))
+    (_, e_l1), (e_s2, e_l2) = err
+    assert e_l2 <= 0.6 * e_l1, err
+    assert e_l2 <= 0.2 * (T0 - Tm), err
+    assert e_s2 <= 0.02 * (Tm - Tw), err
 
 
 def test_neumann_root_known_values():
