@@ -38,6 +38,30 @@ def test_stefan_1000_steps(oracle_mod):
     assert ob_g["solid"] > 30
 
 
+def test_stefan_as_printed_1000_steps(oracle_mod):
+    """Section 4.1 with the temperatures it prints (liquid at T0 = 0.1 above
+    T_m = 0, wall at T_w = -2, W = 5; tests/golden) and rho_s / rho_l = 0.9,
+    so the superheated liquid conducts into the front while the expansion
+    drives a flow: the 1000-step FP32 bar on 200 x 6 cells."""
+    import os
+
+    g = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "stefan_section4_1.txt")) as f:
+        for line in f:
+            kv = line.split("#", 1)[0].split()
+            if len(kv) == 2:
+                g[kv[0]] = float(kv[1])
+    p, phi0, _ = inputs.stefan(nx=200, ny=6, H0=100, Ste=g["Ste_max"], W=g["W"],
+                               T_w=g["T_w"], T_m=g["T_m"])
+    T0 = np.full(phi0.shape, g["T0"])
+    lat, o = _both(oracle_mod, p, phi0, T0, 1000)
+    d = compare_state(lat.get_state(), o.get_state())
+    print("stefan as printed 1000:", d)
+    ob_g, ob_o = lat.observables(), o.observables()
+    assert ob_o["solid"] > 10
+    assert ob_g["solid"] == pytest.approx(ob_o["solid"], rel=1e-5)
+
+
 def test_sessile_ragged_1000_steps(oracle_mod):
     """Sessile drop on the cold wall (density ratio 1000, viscosity ratio 100,
     wetting at 90 deg) on a 100 x 70 lattice: ragged tiles on both axes."""
