@@ -13,6 +13,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_reduce.h"
 
 using lbmk::Inst;
 using lbmk::Item;
@@ -499,7 +500,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
         h->steps++;
     }
     if (n > 0) {
-        cudaError_t e = lbmk::launch_reduce(h->d_inst, h->n_inst, h->d_part, h->d_obs, h->stream);
+        cudaError_t e = lbmk::launch_reduce_obs(h->d_inst, h->n_inst, h->d_part, h->d_obs, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
         h->have_obs = true;

@@ -117,6 +117,23 @@ struct Item {
 // Output columns of one warp strip (the two remaining lanes hold the halo).
 constexpr int kStripW = 30;
 
+// The strip kernels of one storage type ST, row-staged (STAGED) or loading
+// in place, for the supported (warps, regs) pairs; compiled in their own part
+// of the kernel library and reached through the dispatchers below.
+template <typename ST, bool STAGED>
+struct StripPart {
+    static cudaError_t launch(int warps, int regs, const Inst* d_inst, const Item* d_items,
+                              int n_items, int parity, int obs, double* d_partials,
+                              cudaStream_t s);
+    static cudaError_t prepare(int warps, int regs);
+    static int resident_warps(int warps, int regs);
+    static int persist_grid(int warps, int regs, int n_items);
+    static cudaError_t persist_launch(int warps, int regs, int grid, const Inst* d_inst,
+                                      const Item* d_items, int n_items, int parity0, int nsteps,
+                                      unsigned* d_bar, int* d_err, unsigned long long limit_ns,
+                                      cudaStream_t s);
+};
+
 // Launch one time step over every strip item (one warp each, `warps` warps
 // per CTA) in stream s.
 cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_inst,
@@ -164,10 +181,6 @@ cudaError_t launch_barrier_timeout_probe(unsigned* d_bar, int* d_err,
 cudaError_t launch_step(int tx, int ty, int storage, const Inst* d_inst,
                         const Tile* d_tiles, int n_tiles, int parity, int obs,
                         double* d_partials, cudaStream_t s);
-
-// Reduce per-tile partials into one record per lattice (grid = n_inst).
-cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partials,
-                          double* d_obs, cudaStream_t s);
 
 // Double-precision constants of the equilibrium initialisation.
 struct InitConst {

@@ -23,11 +23,27 @@
 // Time levels match the CPU reference: grad p and grad S use the previous
 // step's p and S; d_t(phi u) is a backward difference (Eq. 37).
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "lbm_internal.h"
+
+// The build compiles this file once per part, each compilation whole (nvcc's
+// own partitioning of a file for parallel compilation makes the code of a
+// kernel depend on the rest of the file and on the run), and links the parts:
+//   0  storage dispatch; tile, initialisation and reduction kernels
+//   1  FP32 row-staged strips (plain, observable and persistent steps)
+//   2  FP32 strips that load in place
+//   3  FP16 row-staged strips
+//   4  FP16 strips that load in place
+//   5  BF16 row-staged strips
+// Without LBM_PART the one compilation holds every part.
+#ifndef LBM_PART
+#define LBM_PART -1
+#endif
+#define LBM_HAS_PART(k) (LBM_PART < 0 || LBM_PART == (k))
 
 namespace lbmk {
 namespace {
@@ -1362,6 +1378,7 @@ step_strip_persistent(const Inst* __restrict__ insts, const Item* __restrict__ i
 // A barrier that no other CTA joins: the single CTA of this kernel waits for
 // a count of two until the time limit, raises *err and returns. Used to check
 // that an expired wait is reported to the host rather than hanging.
+#if LBM_HAS_PART(0)
 __global__ void barrier_timeout_probe(unsigned* bar, int* err, unsigned long long limit_ns) {
     grid_barrier(bar, 2u, err, limit_ns);
 }
@@ -1487,7 +1504,7 @@ __global__ void init_16(const Inst* __restrict__ insts, int inst, InitConst c,
     }
 }
 
-// Per-lattice reduction of the per-tile (or per-strip) partials: thread t
+// Reduction of the per-tile partials of the allocation-free step: thread t
 // sums partials t, t + 256, ... in order, then a fixed shared-memory tree
 // combines the 256 sums, so the result does not depend on scheduling. The
 // partials are observable-major, so each observable's loads are coalesced.
@@ -1522,17 +1539,11 @@ __device__ __forceinline__ void reduce_range(int begin, int end,
 }
 
 __global__ void __launch_bounds__(kRedThreads)
-reduce_obs(const Inst* __restrict__ insts, const double* __restrict__ partials,
-           double* __restrict__ out) {
-    const Inst& I = insts[blockIdx.x];
-    reduce_range(I.part_begin, I.part_end, partials, I.part_stride,
-                 out + (long long)blockIdx.x * kObs);
-}
-
-__global__ void __launch_bounds__(kRedThreads)
 reduce_noalloc(int n_parts, const double* __restrict__ partials, double* __restrict__ out) {
     reduce_range(0, n_parts, partials, n_parts, out);
 }
+
+#endif  // LBM_HAS_PART(0)
 
 template <int TX, int TY>
 cudaError_t launch_tile(const Inst* d_inst, const Tile* d_tiles, int n_tiles, int parity,
@@ -1660,17 +1671,18 @@ struct Persist {
     }
 };
 
-// Dispatch of a persistent call F over the supported strip variants, plain
-// (staged == 0) or row-staged with the ring depths of the staged kernels.
+// Dispatch of a persistent call F over the supported strip variants: the
+// row-staged ones (ring depths of the staged kernels) and the plain ones.
 template <typename ST, typename F>
-auto persist_dispatch(int staged, int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 0, ST>())) {
-    if (staged) {
-        if (warps == 4 && regs == 128) return f(Persist<4, 4, 3, ST>());
-        if (warps == 4 && regs == 255) return f(Persist<4, 2, 5, ST>());
-        if (warps == 8 && regs == 128) return f(Persist<8, 2, 3, ST>());
-        if (warps == 2 && regs == 128) return f(Persist<2, 8, 3, ST>());
-        return f(Persist<4, 3, 4, ST>());
-    }
+auto persist_dispatch_staged(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 4, ST>())) {
+    if (warps == 4 && regs == 128) return f(Persist<4, 4, 3, ST>());
+    if (warps == 4 && regs == 255) return f(Persist<4, 2, 5, ST>());
+    if (warps == 8 && regs == 128) return f(Persist<8, 2, 3, ST>());
+    if (warps == 2 && regs == 128) return f(Persist<2, 8, 3, ST>());
+    return f(Persist<4, 3, 4, ST>());
+}
+template <typename ST, typename F>
+auto persist_dispatch_plain(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 0, ST>())) {
     if (warps == 4 && regs == 128) return f(Persist<4, 4, 0, ST>());
     if (warps == 4 && regs == 168) return f(Persist<4, 3, 0, ST>());
     if (warps == 4 && regs == 255) return f(Persist<4, 1, 0, ST>());
@@ -1691,18 +1703,6 @@ cudaError_t launch_strip_st(int warps, int regs, const Inst* d_inst, const Item*
     return cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_inst,
-                              const Item* d_items, int n_items, int parity, int obs,
-                              double* d_partials, cudaStream_t s) {
-    if (n_items <= 0) return cudaSuccess;
-    if (storage == LBM_STORE_FP16)
-        return launch_strip_st<__half>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials, s);
-    if (storage != LBM_STORE_FP32) return cudaErrorNotSupported;
-    return launch_strip_st<float>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials, s);
-}
-
 // BF16 storage is built for the two four-warp staged variants only.
 using bf16 = __nv_bfloat16;
 template <typename F>
@@ -1711,10 +1711,139 @@ auto staged_dispatch_bf16(int regs, F&& f) -> decltype(f(Staged<4, 3, 4, bf16>()
     return f(Staged<4, 3, 4, bf16>());
 }
 template <typename F>
-auto storage_dispatch(int storage, int warps, int regs, F&& f) -> decltype(f(Staged<4, 3, 4, float>())) {
-    if (storage == LBM_STORE_FP16) return staged_dispatch<__half>(warps, regs, f);
-    if (storage == LBM_STORE_BF16) return staged_dispatch_bf16(regs, f);
-    return staged_dispatch<float>(warps, regs, f);
+auto persist_dispatch_bf16(int regs, F&& f) -> decltype(f(Persist<4, 3, 4, bf16>())) {
+    if (regs == 128) return f(Persist<4, 4, 3, bf16>());
+    return f(Persist<4, 3, 4, bf16>());
+}
+
+// The staged or plain strip variants of one storage type, each reached by
+// (warps, regs); the calls check nothing (the dispatchers below do).
+template <typename ST, bool STAGED>
+struct StripKind;
+template <typename ST>
+struct StripKind<ST, true> {
+    template <typename F>
+    static auto on(int warps, int regs, F&& f) {
+        if constexpr (std::is_same_v<ST, bf16>) return staged_dispatch_bf16(regs, f);
+        else return staged_dispatch<ST>(warps, regs, f);
+    }
+    template <typename F>
+    static auto on_persist(int warps, int regs, F&& f) {
+        if constexpr (std::is_same_v<ST, bf16>) return persist_dispatch_bf16(regs, f);
+        else return persist_dispatch_staged<ST>(warps, regs, f);
+    }
+};
+template <typename ST>
+struct StripKind<ST, false> {
+    template <typename F>
+    static auto on_persist(int warps, int regs, F&& f) {
+        return persist_dispatch_plain<ST>(warps, regs, f);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The strip kernels of one storage type and kind, as compiled in their part
+// ---------------------------------------------------------------------------
+#if LBM_PART != 0
+template <typename ST, bool STAGED>
+cudaError_t StripPart<ST, STAGED>::launch(int warps, int regs, const Inst* d_inst,
+                                          const Item* d_items, int n_items, int parity, int obs,
+                                          double* d_partials, cudaStream_t s) {
+    if constexpr (STAGED) {
+        auto go = [&](auto v) {
+            return decltype(v)::launch(d_inst, d_items, n_items, parity, obs, d_partials, s);
+        };
+        return StripKind<ST, true>::on(warps, regs, go);
+    } else {
+        return launch_strip_st<ST>(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials,
+                                   s);
+    }
+}
+
+template <typename ST, bool STAGED>
+cudaError_t StripPart<ST, STAGED>::prepare(int warps, int regs) {
+    if constexpr (STAGED) {
+        auto go = [](auto v) { return decltype(v)::prepare(); };
+        return StripKind<ST, true>::on(warps, regs, go);
+    } else {
+        return cudaSuccess;
+    }
+}
+
+template <typename ST, bool STAGED>
+int StripPart<ST, STAGED>::resident_warps(int warps, int regs) {
+    if constexpr (STAGED) {
+        auto go = [](auto v) { return decltype(v)::resident_warps(); };
+        return StripKind<ST, true>::on(warps, regs, go);
+    } else {
+        if (warps == 4 && regs == 128) return plain_resident_warps<4, 4, ST>();
+        if (warps == 4 && regs == 255) return plain_resident_warps<4, 1, ST>();
+        if (warps == 8 && regs == 128) return plain_resident_warps<8, 2, ST>();
+        if (warps == 2 && regs == 128) return plain_resident_warps<2, 8, ST>();
+        return plain_resident_warps<4, 3, ST>();
+    }
+}
+
+template <typename ST, bool STAGED>
+int StripPart<ST, STAGED>::persist_grid(int warps, int regs, int n_items) {
+    auto g = [&](auto v) { return decltype(v)::grid(n_items); };
+    return StripKind<ST, STAGED>::on_persist(warps, regs, g);
+}
+
+template <typename ST, bool STAGED>
+cudaError_t StripPart<ST, STAGED>::persist_launch(int warps, int regs, int grid,
+                                                  const Inst* d_inst, const Item* d_items,
+                                                  int n_items, int parity0, int nsteps,
+                                                  unsigned* d_bar, int* d_err,
+                                                  unsigned long long limit_ns, cudaStream_t s) {
+    auto go = [&](auto v) {
+        return decltype(v)::launch(grid, d_inst, d_items, n_items, parity0, nsteps, d_bar, d_err,
+                                   limit_ns, s);
+    };
+    return StripKind<ST, STAGED>::on_persist(warps, regs, go);
+}
+#endif
+
+#if LBM_PART == 1
+template struct StripPart<float, true>;
+#elif LBM_PART == 2
+template struct StripPart<float, false>;
+#elif LBM_PART == 3
+template struct StripPart<__half, true>;
+#elif LBM_PART == 4
+template struct StripPart<__half, false>;
+#elif LBM_PART == 5
+template struct StripPart<__nv_bfloat16, true>;
+#endif
+
+// ---------------------------------------------------------------------------
+// Storage dispatch and the tile, initialisation and reduction kernels
+// ---------------------------------------------------------------------------
+#if LBM_HAS_PART(0)
+namespace {
+// F applied to the StripPart of `storage` (FP32, FP16 or BF16) and kind.
+template <bool STAGED, typename F>
+auto on_storage(int storage, F&& f) {
+    if (storage == LBM_STORE_FP16) return f(StripPart<__half, STAGED>());
+    if constexpr (STAGED)
+        if (storage == LBM_STORE_BF16) return f(StripPart<__nv_bfloat16, true>());
+    return f(StripPart<float, STAGED>());
+}
+}  // namespace
+
+cudaError_t launch_step_strip(int warps, int regs, int storage, const Inst* d_inst,
+                              const Item* d_items, int n_items, int parity, int obs,
+                              double* d_partials, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return cudaErrorNotSupported;
+    if (!strip_supported(warps, regs)) return cudaErrorInvalidValue;
+    auto go = [&](auto part) {
+        return decltype(part)::launch(warps, regs, d_inst, d_items, n_items, parity, obs,
+                                      d_partials, s);
+    };
+    return on_storage<false>(storage, go);
 }
 
 bool staged_supported(int warps, int regs, int storage) {
@@ -1723,8 +1852,9 @@ bool staged_supported(int warps, int regs, int storage) {
 }
 
 cudaError_t prepare_staged(int warps, int regs, int storage) {
-    auto go = [](auto v) { return decltype(v)::prepare(); };
-    return storage_dispatch(storage, warps, regs, go);
+    if (!staged_supported(warps, regs, storage)) return cudaErrorInvalidValue;
+    auto go = [&](auto part) { return decltype(part)::prepare(warps, regs); };
+    return on_storage<true>(storage, go);
 }
 
 cudaError_t launch_step_staged(int warps, int regs, int storage, const Inst* d_inst,
@@ -1732,40 +1862,33 @@ cudaError_t launch_step_staged(int warps, int regs, int storage, const Inst* d_i
                                double* d_partials, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     if (!staged_supported(warps, regs, storage)) return cudaErrorInvalidValue;
-    auto go = [&](auto v) {
-        return decltype(v)::launch(d_inst, d_items, n_items, parity, obs, d_partials, s);
+    auto go = [&](auto part) {
+        return decltype(part)::launch(warps, regs, d_inst, d_items, n_items, parity, obs,
+                                      d_partials, s);
     };
-    return storage_dispatch(storage, warps, regs, go);
+    return on_storage<true>(storage, go);
 }
 
 int strip_resident_warps(int staged, int warps, int regs, int storage) {
     if (!strip_supported(warps, regs)) return 0;
+    auto go = [&](auto part) { return decltype(part)::resident_warps(warps, regs); };
     if (staged) {
         if (!staged_supported(warps, regs, storage)) return 0;
-        auto go = [](auto v) { return decltype(v)::resident_warps(); };
-        return storage_dispatch(storage, warps, regs, go);
+        return on_storage<true>(storage, go);
     }
-    if (storage == LBM_STORE_BF16) return 0;  // plain strips: FP32 and FP16
-    auto pick = [&](auto tag) -> int {
-        using ST = decltype(tag);
-        if (warps == 4 && regs == 128) return plain_resident_warps<4, 4, ST>();
-        if (warps == 4 && regs == 255) return plain_resident_warps<4, 1, ST>();
-        if (warps == 8 && regs == 128) return plain_resident_warps<8, 2, ST>();
-        if (warps == 2 && regs == 128) return plain_resident_warps<2, 8, ST>();
-        return plain_resident_warps<4, 3, ST>();
-    };
-    return storage == LBM_STORE_FP16 ? pick(__half()) : pick(float());
+    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return 0;  // plain: FP32, FP16
+    return on_storage<false>(storage, go);
 }
 
 int persistent_grid(int staged, int warps, int regs, int storage, int n_items) {
     if (!strip_supported(warps, regs) || n_items <= 0) return 0;
-    auto g = [&](auto v) { return decltype(v)::grid(n_items); };
-    if (storage == LBM_STORE_BF16) {
-        if (!staged || !staged_supported(warps, regs, storage)) return 0;
-        return regs == 128 ? g(Persist<4, 4, 3, bf16>()) : g(Persist<4, 3, 4, bf16>());
+    auto go = [&](auto part) { return decltype(part)::persist_grid(warps, regs, n_items); };
+    if (staged) {
+        if (!staged_supported(warps, regs, storage)) return 0;
+        return on_storage<true>(storage, go);
     }
-    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(staged, warps, regs, g);
-    return persist_dispatch<float>(staged, warps, regs, g);
+    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return 0;
+    return on_storage<false>(storage, go);
 }
 
 cudaError_t launch_step_strip_persistent(int staged, int warps, int regs, int storage, int grid,
@@ -1774,17 +1897,17 @@ cudaError_t launch_step_strip_persistent(int staged, int warps, int regs, int st
                                          unsigned long long limit_ns, cudaStream_t s) {
     if (!strip_supported(warps, regs) || grid <= 0) return cudaErrorInvalidValue;
     if (n_items <= 0 || nsteps <= 0) return cudaSuccess;
-    auto go = [&](auto v) {
-        return decltype(v)::launch(grid, d_inst, d_items, n_items, parity0, nsteps, d_bar, d_err,
-                                   limit_ns, s);
+    auto go = [&](auto part) {
+        return decltype(part)::persist_launch(warps, regs, grid, d_inst, d_items, n_items,
+                                              parity0, nsteps, d_bar, d_err, limit_ns, s);
     };
-    if (storage == LBM_STORE_BF16) {
-        if (!staged || !staged_supported(warps, regs, storage)) return cudaErrorInvalidValue;
-        return regs == 128 ? go(Persist<4, 4, 3, bf16>()) : go(Persist<4, 3, 4, bf16>());
+    if (staged) {
+        if (!staged_supported(warps, regs, storage)) return cudaErrorInvalidValue;
+        return on_storage<true>(storage, go);
     }
-    if (storage == LBM_STORE_FP16) return persist_dispatch<__half>(staged, warps, regs, go);
-    if (storage != LBM_STORE_FP32) return cudaErrorNotSupported;
-    return persist_dispatch<float>(staged, warps, regs, go);
+    if (storage == LBM_STORE_BF16) return cudaErrorInvalidValue;
+    if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return cudaErrorNotSupported;
+    return on_storage<false>(storage, go);
 }
 
 cudaError_t launch_barrier_timeout_probe(unsigned* d_bar, int* d_err, unsigned long long limit_ns,
@@ -1822,12 +1945,6 @@ cudaError_t launch_step_noalloc(const Inst& I, int tiles_x, int n_tiles, double*
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const Inst* d_inst, int n_inst, const double* d_partials,
-                          double* d_obs, cudaStream_t s) {
-    reduce_obs<<<n_inst, kRedThreads, 0, s>>>(d_inst, d_partials, d_obs);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage, InitConst c,
                         const double* d_phi0, const double* d_T0, int parity, cudaStream_t s) {
     const int threads = 256;
@@ -1844,5 +1961,7 @@ cudaError_t launch_init(const Inst* d_inst, int inst, int n_sites, int storage, 
         return cudaErrorNotSupported;
     return cudaGetLastError();
 }
+
+#endif  // LBM_HAS_PART(0)
 
 }  // namespace lbmk

@@ -16,7 +16,10 @@ from paper_2403_16122_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL32 = 1e-6   # FP32 storage: separately compiled kernels (FMA contraction)
-TOL16 = 2e-5   # FP16 storage: the same, plus a 16-bit rounding that may flip
+# FP16 storage: the same, plus 16-bit roundings that flip and drift apart at
+# the moving interface over the run (measured 2e-4 after 120 steps); a slip in
+# the persistent body's loads or barrier is an error of 1e-2 or more
+TOL16 = 1e-3
 
 
 @pytest.fixture(scope="module")

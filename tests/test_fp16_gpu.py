@@ -82,12 +82,18 @@ def test_fp16_requires_periodic_x_and_strip_layout():
     assert np.isfinite(lat.get_state()[0]).all()
 
 
+STAGED_VARIANTS = [(4, 16, 168), (4, 3, 128), (8, 32, 128), (2, 2, 128), (4, 5, 255), (4, 0, 168)]
+
+
 @pytest.mark.parametrize("case", ["sessile", "bubbles", "periodic"])
 def test_fp16_staged_matches_plain_strip(case):
     """The row-staged strip layout decodes the same 16-bit words as the plain
-    one (separately compiled, so equal to FP32 rounding, which may flip a
-    16-bit rounding now and then): within 2e-5 after 60 steps, for every
-    variant."""
+    one, for every variant, over 60 steps. The kernels are compiled apart and
+    may fuse a different a * b + c into one rounding, so a stored deviation
+    can round to the neighbouring 16-bit value and the two runs drift apart
+    at the moving interface (measured up to 1e-4); a slip in the layout (a
+    word of the wrong plane, half or reference) is an error of 1e-2 or more.
+    The one-step test below bounds the per-step difference itself."""
     from paper_2403_16122_gb300 import lbm
 
     if case == "periodic":
@@ -99,13 +105,42 @@ def test_fp16_staged_matches_plain_strip(case):
     ref.set_kernel(lbm.LBM_KERNEL_STRIP, 4, 16, 168)
     ref.step(60)
     want = ref.get_state()
-    for v in [(4, 16, 168), (4, 3, 128), (8, 32, 128), (2, 2, 128), (4, 5, 255), (4, 0, 168)]:
+    for v in STAGED_VARIANTS:
         lat = gpu_run([p], [(phi0, T0)], 0, storage=lbm.LBM_STORE_FP16)
         lat.set_kernel(lbm.LBM_KERNEL_STAGED, *v)
         lat.step(60)
         got = lat.get_state()
-        assert np.abs(got[0] - want[0]).max() <= 2e-5, v
-        assert np.abs(got[1] - want[1]).max() <= 2e-5, v
+        d = (np.abs(got[0] - want[0]).max(), np.abs(got[1] - want[1]).max())
+        print(case, v, "max |dpop|, |daux| after 60 steps:", d)
+        assert d[0] <= 1e-3 and d[1] <= 1e-3, (v, d)
+
+
+def test_fp16_staged_matches_plain_strip_one_step(oracle_mod):
+    """One step of every staged variant and of the plain strip from one stored
+    FP16 state (the oracle's after 200 steps of a drop with flow): the
+    kernels evaluate the same expressions, so they differ by FP32 rounding
+    and, where that moves a value across a 16-bit rounding boundary, by one
+    unit in the last place of a stored deviation, 2^-10 of it at most (the
+    deviations here stay below 0.02)."""
+    from paper_2403_16122_gb300 import lbm
+
+    p, phi0, T0 = inputs.sessile(nx=80, ny=60, R=20.0, theta_deg=60.0)
+    o = oracle_run(oracle_mod, p, phi0, T0, 200)
+    pops, aux = o.get_state()
+    ref = gpu_run([p], [(phi0, T0)], 0, storage=lbm.LBM_STORE_FP16)
+    ref.set_kernel(lbm.LBM_KERNEL_STRIP, 4, 16, 168)
+    ref.set_state(pops, aux)
+    ref.step(1)
+    want = ref.get_state()
+    for v in STAGED_VARIANTS:
+        lat = gpu_run([p], [(phi0, T0)], 0, storage=lbm.LBM_STORE_FP16)
+        lat.set_kernel(lbm.LBM_KERNEL_STAGED, *v)
+        lat.set_state(pops, aux)  # the same words as ref's
+        lat.step(1)
+        got = lat.get_state()
+        d = (np.abs(got[0] - want[0]).max(), np.abs(got[1] - want[1]).max())
+        print(v, "max |dpop|, |daux| after one step:", d)
+        assert d[0] <= 2e-5 and d[1] <= 2e-5, (v, d)
 
 
 def _crossing_times(t, X, thr):
