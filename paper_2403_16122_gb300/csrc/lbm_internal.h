@@ -52,6 +52,14 @@ struct Bits16<__half> {
     static __host__ __device__ __half from_d(double v) { return __double2half(v); }
     static __host__ __device__ __half from_bits(unsigned short b) { return __ushort_as_half(b); }
     static __host__ __device__ unsigned short bits(__half v) { return __half_as_ushort(v); }
+    // two values in one word (lo in the low half), and back, one rounding each
+    static __device__ unsigned pack2(float lo, float hi) {
+        const __half2 q = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const unsigned*>(&q);
+    }
+    static __device__ float2 unpack2(unsigned w) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    }
 };
 template <>
 struct Bits16<__nv_bfloat16> {
@@ -60,6 +68,13 @@ struct Bits16<__nv_bfloat16> {
     static __host__ __device__ __nv_bfloat16 from_d(double v) { return __double2bfloat16(v); }
     static __host__ __device__ __nv_bfloat16 from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
     static __host__ __device__ unsigned short bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+    static __device__ unsigned pack2(float lo, float hi) {
+        const __nv_bfloat162 q = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const unsigned*>(&q);
+    }
+    static __device__ float2 unpack2(unsigned w) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    }
 };
 __host__ __device__ inline int gh_at(int i, int plane, int site, int set) {
     return 2 * (i - 1) * plane + 2 * site + set;

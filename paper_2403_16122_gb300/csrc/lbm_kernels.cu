@@ -509,12 +509,13 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                 const Ref& d = dref[i];
                 const float dg = gn - w * d.phi, dh = hn - w * P.Cpref * d.T;
                 const float df = (fn - f_rest(i, pn)) * kFScale;
-                const ST qg = C16::from_f(dg), qh = C16::from_f(dh), qf = C16::from_f(df);
-                *reinterpret_cast<unsigned*>(B + gh_at(i, plane, own, 0)) =
-                    (unsigned)C16::bits(qg) | ((unsigned)C16::bits(qh) << 16);
+                const unsigned qgh = C16::pack2(dg, dh);  // (g_i, h_i) in one word
+                const ST qf = C16::from_f(df);
+                *reinterpret_cast<unsigned*>(B + gh_at(i, plane, own, 0)) = qgh;
                 B[f_at(i, plane, own)] = C16::bits(qf);
-                eg += dg - C16::to_f(qg);
-                eh += dh - C16::to_f(qh);
+                const float2 rgh = C16::unpack2(qgh);
+                eg += dg - rgh.x;
+                eh += dh - rgh.y;
                 ef += df - C16::to_f(qf);
             }
         }
@@ -984,6 +985,27 @@ __device__ __forceinline__ void staged_set(const float* slot, int lane, int r, i
     }
 }
 
+// Sets g and h of a staged row together (16-bit storage): each (g_i, h_i)
+// word is loaded once and decoded by one paired conversion, then treated as
+// staged_set treats it.
+template <typename ST>
+__device__ __forceinline__ void staged_gh(const float* slot, int lane, int r, int ny, bool py,
+                                          int flags, float abb, float g[9], float h[9],
+                                          const Ref& ref, float Cpref) {
+    const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
+    const bool dir = (wlo && (flags & kDirYlo)) || (whi && (flags & kDirYhi));
+    g[0] = slot[4 * lane];
+    h[0] = slot[4 * lane + 1];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const float2 raw = Bits16<ST>::unpack2(__float_as_uint(slot[slot_gh(i, lane)]));
+        g[i] = raw.x + WGT(i) * ref.phi;
+        h[i] = raw.y + WGT(i) * Cpref * ref.T;
+        const bool wall = (CY(i) > 0 && wlo) || (CY(i) < 0 && whi);
+        if (wall && dir) h[i] = -h[i] + 2.0f * WGT(i) * abb;
+    }
+}
+
 // One warp advances strip item W by one step (the body of every strip kernel).
 // STG = 0: populations are loaded where they are consumed; STG >= 3: rows are
 // staged through `ring` (STG slots of this warp): while row y is computed,
@@ -1080,15 +1102,15 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         float gg[9], hh[9];
         const float* sl = slot(j);
         r = slot_ref(sl);
-        staged_set<0, ST>(sl, lane, y, ny, c.py, l.flags, abb, gg, par, r, P.Cpref);
-        staged_set<1, ST>(sl, lane, y, ny, c.py, l.flags, abb, hh, par, r, P.Cpref);
-        if constexpr (kHalf) {  // keep the decoded values for the collision
-            float* ws = const_cast<float*>(sl);
+        if constexpr (kHalf) {
+            staged_gh<ST>(sl, lane, y, ny, c.py, l.flags, abb, gg, hh, r, P.Cpref);
+            float* ws = const_cast<float*>(sl);  // the decoded values, for the collision
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                ws[slot_gh(i, lane)] = gg[i];
-                ws[slot_gh(i, lane) + 1] = hh[i];
-            }
+            for (int i = 1; i < 9; ++i)
+                *reinterpret_cast<float2*>(ws + slot_gh(i, lane)) = make_float2(gg[i], hh[i]);
+        } else {
+            staged_set<0, ST>(sl, lane, y, ny, c.py, l.flags, abb, gg, par, r, P.Cpref);
+            staged_set<1, ST>(sl, lane, y, ny, c.py, l.flags, abb, hh, par, r, P.Cpref);
         }
         m = local_macro(P, gg, hh, sl[4 * lane + 3]);
         p = sl[kSlotO1 + 4 * lane + 2];
