@@ -156,6 +156,7 @@ struct lbm_handle {
     Tile* d_tiles = nullptr;
     double* d_part = nullptr;
     double* d_obs = nullptr;
+    double* h_obs = nullptr;   // pinned host mirror of d_obs (null: copy to the caller directly)
     double* d_stage = nullptr;
     int parity = 0;
     int64_t steps = 0;
@@ -172,6 +173,9 @@ struct lbm_handle {
     bool failed = false;               // a barrier wait ran out: state is not usable
     cudaStream_t cap_stream = nullptr; // private stream for graph capture
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // `chunk` steps from parity 0 / 1
+    ~lbm_handle() {
+        if (h_obs) cudaFreeHost(h_obs);
+    }
 };
 
 namespace {
@@ -360,6 +364,18 @@ cudaError_t sync_checked(lbm_handle* h) {
     return cudaSuccess;
 }
 
+// n doubles of the observable records from offset off to the caller's out,
+// through the pinned mirror (the driver stages a copy into pageable memory
+// with an extra synchronisation), then the synchronising check.
+cudaError_t read_obs(lbm_handle* h, size_t off, size_t n, double* out) {
+    double* dst = h->h_obs ? h->h_obs + off : out;
+    cudaError_t e = cudaMemcpyAsync(dst, h->d_obs + off, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = sync_checked(h);
+    if (e == cudaSuccess && h->h_obs) memcpy(out, dst, n * sizeof(double));
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -403,6 +419,10 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
     h->d_obs = reinterpret_cast<double*>(h->ws + h->layout.obs_off);
     h->d_stage = reinterpret_cast<double*>(h->ws + h->layout.stage_off);
     h->d_sync = reinterpret_cast<SyncBlock*>(h->ws + h->layout.sync_off);
+    if (cudaMallocHost(&h->h_obs, sizeof(double) * lbmk::kObs * n_inst) != cudaSuccess) {
+        h->h_obs = nullptr;  // the observables are then copied to the caller's memory directly
+        cudaGetLastError();
+    }
     if (cudaMemsetAsync(h->d_sync, 0, sizeof(SyncBlock), h->stream) != cudaSuccess) {
         delete h;
         return LBM_ECUDA;
@@ -511,9 +531,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
 int lbm_observables_all(lbm_handle* h, double* out) {
     if (!h || !out) return LBM_EINVAL;
     if (!h->have_obs) return LBM_ESTATE;
-    cudaError_t e = cudaMemcpyAsync(out, h->d_obs, sizeof(double) * lbmk::kObs * h->n_inst,
-                                    cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = sync_checked(h);
+    cudaError_t e = read_obs(h, 0, (size_t)lbmk::kObs * h->n_inst, out);
     if (e != cudaSuccess) return cuda_fail(e);
     if (h->failed) return LBM_ETIMEOUT;
     for (int k = 0; k < h->n_inst; ++k)
@@ -524,9 +542,7 @@ int lbm_observables_all(lbm_handle* h, double* out) {
 int lbm_observables(lbm_handle* h, int32_t inst, double* out) {
     if (!inst_ok(h, inst) || !out) return LBM_EINVAL;
     if (!h->have_obs) return LBM_ESTATE;
-    cudaError_t e = cudaMemcpyAsync(out, h->d_obs + (size_t)inst * lbmk::kObs,
-                                    sizeof(double) * lbmk::kObs, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = sync_checked(h);
+    cudaError_t e = read_obs(h, (size_t)inst * lbmk::kObs, lbmk::kObs, out);
     if (e != cudaSuccess) return cuda_fail(e);
     if (h->failed) return LBM_ETIMEOUT;
     return out[LBM_OBS_NONFINITE] > 0 ? LBM_EUNSTABLE : LBM_OK;
