@@ -383,7 +383,50 @@ struct ObsAcc {
         c[j] += fabsf(s[j]) >= fabsf(x) ? (s[j] - t) + x : (x - t) + s[j];
         s[j] = t;
     }
+    __device__ __forceinline__ void max(int j, float x) { s[j] = fmaxf(s[j], x); }
     __device__ __forceinline__ double total(int j) const { return (double)s[j] + (double)c[j]; }
+};
+
+// Observable sums of a warp strip, taken row by row: at the end of each row
+// the values of its sites are summed across the warp (a fixed xor tree in
+// FP32, at most 30 sites), and lane j carries observable j's running sum over
+// the rows with Neumaier's compensation, so a lane keeps two running values
+// instead of 2 kObs. Lanes that update no site contribute zeros; slot 9 is a
+// maximum.
+struct RowObs {
+    float v[kObs];
+    float s, c;
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) v[j] = 0.f;
+        s = 0.f;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void add(int j, float x) { v[j] += x; }
+    __device__ __forceinline__ void max(int j, float x) { v[j] = fmaxf(v[j], x); }
+    // all 32 lanes, once per row
+    __device__ __forceinline__ void flush(int lane) {
+        float mine = 0.f;
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) {
+            float t = v[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float u = __shfl_xor_sync(0xffffffffu, t, o);
+                t = (j == 9) ? fmaxf(t, u) : t + u;
+            }
+            mine = lane == j ? t : mine;
+            v[j] = 0.f;
+        }
+        if (lane == 9) {
+            s = fmaxf(s, mine);
+        } else {
+            const float t = s + mine;
+            c += fabsf(s) >= fabsf(mine) ? (s - t) + mine : (mine - t) + s;
+            s = t;
+        }
+    }
+    __device__ __forceinline__ double total() const { return (double)s + (double)c; }
 };
 
 // Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
@@ -391,13 +434,13 @@ struct ObsAcc {
 // post-collision populations and carried fields of one site. The order of
 // every floating-point operation is fixed here, so all kernels built on it
 // produce bit-identical results.
-template <bool OBS, typename ST = float, typename Pops = ArrPops>
+template <bool OBS, typename ST = float, typename Pops = ArrPops, typename Acc = ObsAcc>
 __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macro& m,
                                             const Pops& pop,
                                             float phiux_p, float phiuy_p, const Stencil& st,
                                             void* __restrict__ Bv, float* __restrict__ Baux,
                                             int plane, int own, bool on_col, bool on_row,
-                                            ObsAcc& ob, const Ref* dref = nullptr) {
+                                            Acc& ob, const Ref* dref = nullptr) {
     const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
     const float gphx = st.gphx, gphy = st.gphy, lph = st.lph, grx = st.grx, gry = st.gry;
     const float gpx = st.gpx, gpy = st.gpy, gSx = st.gSx, gSy = st.gSy;
@@ -544,7 +587,7 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         ob.add(6, phi * mdot);
         if (on_col) ob.add(7, fs);
         if (on_row) ob.add(8, fs);
-        ob.s[9] = fmaxf(ob.s[9], sqrtf(uu));
+        ob.max(9, sqrtf(uu));
         const bool bad = !isfinite(phi) || !isfinite(m.Hp) || !isfinite(ux) || !isfinite(uy) ||
                          !isfinite(pn);
         if (bad) ob.add(10, 1.f);
@@ -1118,7 +1161,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         note_outer(y);
     };
 
-    ObsAcc ob;
+    RowObs ob;
     if (OBS) ob.zero();
 
     // rows y-1 (m), y (0) and y+1 (p) of phi, rho, p^{n-1}, S^{n-1} (and T)
@@ -1277,6 +1320,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
                                  l.plane, own, c.xc == nx / 2, y == ny / 2, ob, dref);
         }
 
+        if (OBS) ob.flush(lane);
+
         // advance the window
         phm = ph0; ph0 = php; rhm = rh0; rh0 = rhp;
         pm = p0; p0 = pp; Sm = S0; S0 = Sp;
@@ -1286,18 +1331,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     }
     if constexpr (STG > 0) cp_async_wait<0>();  // the trailing groups are empty
 
-    if (OBS) {
-#pragma unroll
-        for (int j = 0; j < kObs; ++j) {
-            double v = ob.total(j);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double u = __shfl_xor_sync(0xffffffffu, v, o);
-                v = (j == 9) ? fmax(v, u) : v + u;
-            }
-            if (lane == 0) partials[(long long)j * I.part_stride + W.part] = v;
-        }
-    }
+    if (OBS && lane < kObs) partials[(long long)lane * I.part_stride + W.part] = ob.total();
 }
 
 template <int WARPS, int MINB, bool OBS, typename ST>
