@@ -30,7 +30,9 @@
  * Ownership: the caller owns the device workspace passed to lbm_create (the
  * library never allocates device memory) and every host array; host arrays
  * are read or written during the call and never retained. The handle itself
- * is host memory owned by the library until lbm_destroy.
+ * is host memory owned by the library until lbm_destroy, with a pinned host
+ * mirror of the observable records (11 doubles per lattice) through which
+ * lbm_observables and lbm_observables_all copy.
  *
  * Thread safety: a handle is used by one host thread at a time. All device
  * work is queued on the stream given to lbm_create.
@@ -142,7 +144,8 @@ int lbm_workspace_size(const lbm_params* p, int32_t n_inst, int32_t storage,
 /* Create a handle over n_inst independent lattices (the paper's problem
    statement per lattice, Section 4). d_workspace is caller-owned device
    memory of at least lbm_workspace_size bytes, 256-byte aligned; the library
-   carves every device buffer from it and never allocates. cuda_stream is a
+   carves every device buffer from it and never allocates device memory (the
+   handle's pinned observable mirror is host memory). cuda_stream is a
    cudaStream_t (NULL for the legacy default stream). Uploads the tile and
    instance tables (host-to-device copies on the stream). On success *out
    holds the handle; the fields still need lbm_init_fields. */
