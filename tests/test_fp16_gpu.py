@@ -234,3 +234,33 @@ def test_bf16_one_step_from_common_state(oracle_mod):
     assert np.abs(ga - oa).max() < 4e-4
     with pytest.raises(lbm.LbmError):
         lat.set_kernel(lbm.LBM_KERNEL_STRIP, 4, 16, 168)  # BF16: staged strips only
+
+
+def test_16bit_storage_at_benchmark_size():
+    """The precision bar at the benchmark's own size and length: the 1024 x
+    1024 drop with 8 bubbles on the cold wall, 100,000 steps (the front moves
+    some 40 cells), in FP16 and BF16 storage against FP32 storage on the same
+    GPU: front height at the centre column within 0.5 lu, solidified amount
+    and volume within 1 %."""
+    from paper_2403_16122_gb300 import lbm
+
+    p, phi0, T0 = inputs.bubbles_drop(n=1024)
+    steps = 100_000
+    res = {}
+    for name, st in (("fp32", lbm.LBM_STORE_FP32), ("fp16", lbm.LBM_STORE_FP16),
+                     ("bf16", lbm.LBM_STORE_BF16)):
+        lat = gpu_run([p], [(phi0, T0)], 0, storage=st)
+        lat.step(steps)
+        res[name] = lat.observables()
+        lat.close()
+    ref = res["fp32"]
+    assert ref["solid_col"] > 30 and ref["nonfinite"] == 0
+    for name in ("fp16", "bf16"):
+        o = res[name]
+        d = {"front": o["solid_col"] - ref["solid_col"],
+             "solid": o["solid"] / ref["solid"] - 1.0,
+             "volume": o["volume"] / ref["volume"] - 1.0}
+        print(name, "after", steps, "steps at 1024x1024 against FP32:", d,
+              {k: (o[k], ref[k]) for k in ("solid_col", "solid", "volume")})
+        assert abs(d["front"]) <= 0.5, (name, d)
+        assert abs(d["solid"]) <= 0.01 and abs(d["volume"]) <= 0.01, (name, d)
