@@ -429,6 +429,25 @@ def run_ours(args, dist: Dist):
                                "relative_to_plain": ms_per_step / msb}
         latb.close()
 
+    # the Stefan problem of Section 4.1 (256 x 8 cells, walls in x: the tile
+    # kernel): 2048 sites a step, so launch-bound; one launch per step against
+    # runs of steps replayed from a CUDA graph
+    if forms is not None:
+        ps, phis, Ts = inputs.stefan()
+        st_out = {}
+        for name, mode in (("launch", lbm.LBM_EXEC_LAUNCH), ("graph", lbm.LBM_EXEC_GRAPH)):
+            lats = lbm.Lattice([ps], device=dev)
+            lats.init(phis, Ts)
+            lats.set_exec(mode, 500)
+            lats.step(501)
+            mss = _timed_steps(lats, 5000)
+            st_out[name] = {"value": ps["nx"] * ps["ny"] / (mss * 1e-3) / 1e6, "ms_per_step": mss,
+                            "kernel": list(lats.kernel)}
+            lats.close()
+        forms["stefan_256x8"] = {"value": max(v["value"] for v in st_out.values()), "unit": "MLUPS",
+                                 "steps": 5000, **st_out,
+                                 "what": "launch-bound: 2048 sites a step"}
+
     if forms is not None and not args.no_batched:
         forms.update(batched_forms(args, dev, peak))
 

@@ -26,6 +26,31 @@ def _both(oracle_mod, p, phi0, T0, steps):
     return lat, o
 
 
+@pytest.mark.parametrize("ste", [0.1, 0.2])
+def test_stefan_front_follows_neumann_for_20000_steps(ste):
+    """The Stefan problem of Section 4.1 run on the GPU for its full length,
+    the front read every 100 steps: from t = 2000 on it follows the one-phase
+    Neumann solution s = 2 lambda sqrt(alpha t), lambda exp(lambda^2)
+    erf(lambda) = Ste / sqrt(pi), within 1 lu (the enthalpy front is smeared
+    over about a cell)."""
+    from scipy.optimize import brentq
+    from scipy.special import erf
+
+    lam = brentq(lambda l: l * math.exp(l * l) * erf(l) - ste / math.sqrt(math.pi), 1e-9, 3.0)
+    p, phi0, T0 = inputs.stefan(Ste=ste)
+    alpha = (p["tau_h"] - 0.5) / 3.0
+    lat = gpu_run([p], [(phi0, T0)], 0)
+    worst = 0.0
+    for k in range(1, 201):
+        lat.step(100)
+        t = 100 * k
+        s = lat.observables()["solid"] / p["ny"]
+        if t >= 2000:
+            worst = max(worst, abs(s - 2 * lam * math.sqrt(alpha * t)))
+    print("Ste", ste, "worst |s - s_Neumann| for 2000 <= t <= 20000:", worst, "final s", s)
+    assert worst <= 1.0
+
+
 def test_stefan_1000_steps(oracle_mod):
     """Three-phase Stefan problem, 256 x 8, the 1000-step FP32 bar."""
     p, phi0, T0 = inputs.stefan()
