@@ -365,6 +365,24 @@ struct SlotPops {
     }
 };
 
+// Row-staged 16-bit strips: g and h decoded in the slot, f decoded into
+// registers just before the collision.
+struct SlotGHPops {
+    const float* s;
+    int lane;
+    const float* f;
+    __device__ __forceinline__ float rd(int off) const {
+        return *reinterpret_cast<const volatile float*>(s + off);
+    }
+    __device__ __forceinline__ float G(int i) const {
+        return rd(i == 0 ? 4 * lane : 256 + 64 * (i - 1) + 2 * lane);
+    }
+    __device__ __forceinline__ float H(int i) const {
+        return rd(i == 0 ? 4 * lane + 1 : 256 + 64 * (i - 1) + 2 * lane + 1);
+    }
+    __device__ __forceinline__ float F(int i) const { return f[i]; }
+};
+
 // Per-thread observable sums of the sites it updates. The sums run in FP32
 // with Neumaier's compensation (the running sum and the rounding error each
 // addition dropped), and (s + c) is taken in FP64 before the warp, block and
@@ -1248,14 +1266,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             phm = strip_wet_ghost(ph0, php, oB0, oB1, lane, P.tan_w);
             rhm = rh0; pm = p0; Sm = S0; tm = t0;
         }
-        if constexpr (kHalf) {
-            pull_f();
-            if constexpr (STG > 0) {  // decoded f for the collision's slot reads
-                float* ws = slot(jy);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) ws[slot_f(i, lane)] = f[i];
-            }
-        }
+        if constexpr (kHalf && STG == 0) pull_f();
 
         // Eq. 38 from column sums exchanged with the neighbouring lanes
         Stencil st;
@@ -1293,9 +1304,15 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
             }
         }
 
-        if constexpr (kSlotPops) {
+        if constexpr (kSlotPops && kHalf) {
+            pull_f();  // all lanes (shuffles); f stays in registers for the collision
+            if (out_lane)
+                site_update<OBS, ST>(P, l.flags, mO, SlotGHPops{slot(jy), lane, f}, phiux_p,
+                                     phiuy_p, st, B, Baux, l.plane, own, c.xc == nx / 2,
+                                     y == ny / 2, ob, dref);
+        } else if constexpr (kSlotPops) {
             if (out_lane) {
-                int hmask = 0;  // FP16: applied when the slot was decoded
+                int hmask = 0;
                 if (!kHalf && !c.py) {
                     const bool lo = y == 0 && (l.flags & kDirYlo), hi = y == ny - 1 && (l.flags & kDirYhi);
 #pragma unroll
