@@ -194,17 +194,19 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+    """(DRAM bytes per launch, the kernel they were counted on) of the step
+    kernel from the committed ncu summary, if it was taken on the current
+    kernel source; else (None, None)."""
     path = os.path.join(ROOT, "profiles", f"step_{workload}.md")
     try:
         txt = open(path).read()
     except OSError:
-        return None
+        return None, None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+kernel_source:\s*([0-9a-f]+)", txt)
     if not m or m.group(2) != kernel_source_hash():
-        return None
-    return float(m.group(1))
+        return None, None
+    k = re.search(r"Kernel: `([^`]+)`", txt)
+    return float(m.group(1)), (k.group(1) if k else None)
 
 
 # ---------------------------------------------------------------------------
@@ -331,9 +333,12 @@ def run_ours(args, dist: Dist):
     # roofline of the dominant kernel (the fused step), from the same events
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_lu * sites / (ms / args.steps * 1e-3) / 1e9
-    traffic = profiled_traffic(workload)
+    traffic, traffic_kernel = profiled_traffic(workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
+                # the variant the counters were taken on (the autotuner may pick
+                # a sibling with the same items and ring: the same traffic)
+                "traffic_kernel": traffic_kernel,
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_lu * sites}
 
