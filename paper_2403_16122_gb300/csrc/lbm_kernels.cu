@@ -924,7 +924,7 @@ __device__ __forceinline__ float strip_wet_ghost(float a, float b, float outer_a
 // f_l), 128 + 4l + c ((phi u)_x, (phi u)_y, p, S), 256 + 64 (i - 1) + 2l + s
 // the pair (g_i, h_i), 768 + 32 (i - 1) + l f_i, and for FP16 storage
 // 1024 + 2l + c (phi_ref, T_ref). FP16 pairs and f_i arrive as the aligned
-// 32-bit word that holds them; decoded values are written back in place.
+// 32-bit word holding them; decoded pairs go back over it, f_i to registers.
 // ---------------------------------------------------------------------------
 constexpr int kSlotO1 = 128, kSlotGH = 256, kSlotF = 768, kSlotR = 1024;
 __device__ __forceinline__ int slot_gh(int i, int lane) { return kSlotGH + 64 * (i - 1) + 2 * lane; }
@@ -1078,7 +1078,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     constexpr bool kHalf = sizeof(ST) != 4;
     static_assert(STG == 0 || STG >= 3, "staging needs at least three ring slots");
     // Staging: the collision reads its populations from the ring slot (FP16:
-    // the decoded values, written back over the staged words)
+    // g, h decoded over the staged words; f decoded into registers)
     constexpr bool kSlotPops = STG > 0;
     const int lane = threadIdx.x & 31;
     const Inst& I = insts[W.inst];
