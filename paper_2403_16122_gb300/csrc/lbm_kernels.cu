@@ -946,6 +946,27 @@ __device__ __forceinline__ void cp_async16(float* dst_smem, const float* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
+// The same copies with an L2 eviction priority (createpolicy below).
+template <int N>
+__device__ __forceinline__ void cp_async_p(float* dst_smem, const float* src,
+                                           unsigned long long pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;" ::"r"(d),
+                 "l"(src), "n"(N), "l"(pol)
+                 : "memory");
+}
+// L2 priority of a staged row: 1 keep (evict last), 2 release (evict first),
+// otherwise normal.
+__device__ __forceinline__ unsigned long long l2_policy(int hint) {
+    unsigned long long pol;
+    if (hint == 1)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else if (hint == 2)
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -956,10 +977,14 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Issue the copies of lattice row r (possibly -1 or ny for periodic y) into
 // this lane's part of the ring slot at `slot`. macro_only: only what the
-// local macroscopic step needs (everything but f_i).
+// local macroscopic step needs (everything but f_i). hint: the rows an item
+// shares with the item below it are read by this item first and by that one
+// at the end of the step; they are kept in L2 (1) until then and released (2)
+// by the second read.
 template <typename ST, bool NC>
 __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, int xm, int xp,
-                                          bool py, int r, bool macro_only, float* slot) {
+                                          bool py, int r, bool macro_only, float* slot,
+                                          int hint = 0) {
     constexpr bool kHalf = sizeof(ST) != 4;
     const int ny = l.ny, plane = l.plane;
     const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
@@ -967,9 +992,10 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, i
     const int ym = rr == 0 ? ny - 1 : rr - 1, yp = rr == ny - 1 ? 0 : rr + 1;
     const int o0 = rr * l.pitch, om = ym * l.pitch, op = yp * l.pitch;
     const int own = o0 + xc;
-    cp_async16(slot + 4 * lane, l.Aaux + own0_at(own, 0));
-    cp_async16(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(plane, own, 0));
-    if constexpr (kHalf) cp_async8(slot + kSlotR + 2 * lane, l.Aaux + ref_at(plane, own, 0));
+    const unsigned long long pol = l2_policy(hint);
+    cp_async_p<16>(slot + 4 * lane, l.Aaux + own0_at(own, 0), pol);
+    cp_async_p<16>(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(plane, own, 0), pol);
+    if constexpr (kHalf) cp_async_p<8>(slot + kSlotR + 2 * lane, l.Aaux + ref_at(plane, own, 0), pol);
     const unsigned short* A16 = reinterpret_cast<const unsigned short*>(l.A);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -981,14 +1007,15 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, i
         if constexpr (kHalf) {
             // planes and rows hold an even number of 16-bit values, so every
             // aligned word lies inside its row
-            cp_async4(slot + slot_gh(i, lane),
-                      reinterpret_cast<const float*>(A16 + gh_at(si, plane, site, 0)));
+            cp_async_p<4>(slot + slot_gh(i, lane),
+                          reinterpret_cast<const float*>(A16 + gh_at(si, plane, site, 0)), pol);
             if (!macro_only)
-                cp_async4(slot + slot_f(i, lane),
-                          reinterpret_cast<const float*>(A16 + (f_at(si, plane, site) & ~1)));
+                cp_async_p<4>(slot + slot_f(i, lane),
+                              reinterpret_cast<const float*>(A16 + (f_at(si, plane, site) & ~1)),
+                              pol);
         } else {
-            cp_async8(slot + slot_gh(i, lane), l.A + gh_at(si, plane, site, 0));
-            if (!macro_only) cp_async4(slot + slot_f(i, lane), l.A + f_at(si, plane, site));
+            cp_async_p<8>(slot + slot_gh(i, lane), l.A + gh_at(si, plane, site, 0), pol);
+            if (!macro_only) cp_async_p<4>(slot + slot_f(i, lane), l.A + f_at(si, plane, site), pol);
         }
     }
 }
@@ -1149,7 +1176,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         if constexpr (STG > 0) {
             if (j < R && (j > 0 || has_lo) && (j < R - 1 || has_hi))
                 stage_row<ST>(l, lane, c.xc, c.xm, c.xp, c.py, y0 - 1 + j, j == 0 || j == R - 1,
-                              slot(j));
+                              slot(j), j <= 1 ? 1 : (j >= R - 2 ? 2 : 0));
             cp_async_commit();  // possibly empty: one group per ring index
         }
     };
