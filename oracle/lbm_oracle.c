@@ -71,6 +71,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* D2Q9 velocities and weights, Eqs. 22-23: i = 1..4 point E, N, W, S and
    i = 5..8 point NE, NW, SW, SE. */
@@ -96,6 +99,7 @@ struct oracle_state {
     double *pre;           /* 27 planes, post-streaming (pre-collision) */
     double *fld;           /* 10 planes of the step's macroscopic fields */
     double *pre_fl;        /* liquid fraction of the step */
+    double mdot_int;       /* sum over steps and sites of mdot (Eq. 19) */
 };
 
 static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
@@ -421,6 +425,7 @@ int oracle_init(oracle_state* s, const double* phi0, const double* T0) {
         F[ORACLE_FLD_S * n + k] = 0.0;
     }
     s->step = 0;
+    s->mdot_int = 0.0;
     return 0;
 }
 
@@ -450,12 +455,14 @@ static void step_once(oracle_state* s) {
        post-collision population one link along c_i. */
     for (int set = 0; set < 3; ++set)
         for (int i = 0; i < 9; ++i)
+#pragma omp parallel for
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x)
                     s->pre[(int64_t)(set * 9 + i) * n + site(s, x, y)] =
                         pull(s, s->pop, set, i, x, y);
 
     /* (2) Local macroscopic fields at the new time level. */
+#pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int64_t k = site(s, x, y);
@@ -480,6 +487,7 @@ static void step_once(oracle_state* s) {
         }
 
     /* (3) Gradients, forces, flow macroscopics and the three collisions. */
+#pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             int64_t k = site(s, x, y);
@@ -576,6 +584,10 @@ static void step_once(oracle_state* s) {
             F[ORACLE_FLD_S * n + k] = S;
         }
 
+    /* The mass-source integral: this step's mdot of every site, in site
+       order, added to the running FP64 sum. */
+    for (int64_t k = 0; k < n; ++k) s->mdot_int += mdf[k];
+
     double* t = s->pop; s->pop = s->pop_new; s->pop_new = t;
     t = s->aux; s->aux = s->aux_new; s->aux_new = t;
     s->step += 1;
@@ -588,12 +600,28 @@ int oracle_step(oracle_state* s, int64_t n) {
 
 int64_t oracle_step_count(const oracle_state* s) { return s->step; }
 
+/* Host threads of the site loops (OpenMP over lattice rows; each site's
+   result depends only on the previous state, so the thread count does not
+   change any value). Without OpenMP the oracle is single-threaded. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 void oracle_get_state(const oracle_state* s, double* pops, double* aux) {
     if (pops) memcpy(pops, s->pop, sizeof(double) * 27 * (size_t)s->n);
     if (aux) memcpy(aux, s->aux, sizeof(double) * AUX_COUNT * (size_t)s->n);
 }
 
+double oracle_mdot_integral(const oracle_state* s) { return s->mdot_int; }
+
 void oracle_set_state(oracle_state* s, const double* pops, const double* aux) {
+    s->mdot_int = 0.0; /* a new run */
     if (pops) memcpy(s->pop, pops, sizeof(double) * 27 * (size_t)s->n);
     if (aux) memcpy(s->aux, aux, sizeof(double) * AUX_COUNT * (size_t)s->n);
 }

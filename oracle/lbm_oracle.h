@@ -97,6 +97,12 @@ void oracle_destroy(oracle_state* s);
 int  oracle_init(oracle_state* s, const double* phi0, const double* T0);
 int  oracle_step(oracle_state* s, int64_t n);
 int64_t oracle_step_count(const oracle_state* s);
+/* Threads of the site loops: n > 0 sets them; returns the count in effect
+   (1 without OpenMP). */
+int oracle_set_threads(int n);
+/* Sum over every step since oracle_init / oracle_set_state and every site of
+   mdot (Eq. 19): the mass-source integral. */
+double oracle_mdot_integral(const oracle_state* s);
 /* pops: 27*nx*ny, aux: 5*nx*ny (layouts above). */
 void oracle_get_state(const oracle_state* s, double* pops, double* aux);
 void oracle_set_state(oracle_state* s, const double* pops, const double* aux);

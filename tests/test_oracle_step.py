@@ -446,3 +446,56 @@ def test_boussinesq_hydrostatic_balance(oracle_mod, T0):
     expected = -rho0 * (-g) * beta * (T0 - Tref)
     assert slope == pytest.approx(expected, rel=1e-3)
     assert np.abs(f["uy"]).max() < 1e-5 and np.abs(f["ux"]).max() < 1e-12
+
+
+def test_solid_forcing_stops_a_frozen_block_in_one_step(oracle_mod):
+    """Eqs. 30-35 with the solid interaction force f = f_s (u_s - u*) / dt,
+    u_s = 0 (Section 3.3): in a fully solid periodic block (f_s = 1, no phase
+    change, uniform phi = 1) carrying a uniform flow u0 in its f populations,
+    u* = u0, f = -u0, u = u0 / 2 and rho f enters F_i with the factor
+    (1 - 1/(2 tau_f)) of Eq. 30. The post-collision momentum is then
+    rho u0 - (rho u0 - rho u0 / 2) / tau_f - (1 - 1/(2 tau_f)) rho u0 = 0 for
+    any tau_f: exactly zero after one step. Reading the force as 2 f_s (u_s -
+    u*), dropping rho from rho f, or dropping the (1 - 1/(2 tau_f)) factor
+    each leaves a momentum of order rho u0."""
+    nx, ny = 6, 5
+    for tau_f in (0.7, 1.3):
+        p = inputs.params(nx=nx, ny=ny, tau_f_liquid=tau_f, rho_ratio_sl=0.9)
+        o = oracle_mod.Oracle(p)
+        rho_s = o.derived()["rho_s"]
+        T = -0.5                      # H = Cp T < H_s = Cp T_m: solid, f_l = 0
+        u0 = (0.03, -0.02)
+        pops = np.zeros((27, ny, nx))
+        pops[0:9] = oracle_mod.geq(1.0, 0.0, 0.0)[:, None, None]
+        pops[9:18] = oracle_mod.heq(p["Cp"] * T, T, 1.0, 1.0, 0.0, 0.0)[:, None, None]
+        pops[18:27] = oracle_mod.feq(0.0, rho_s, *u0)[:, None, None]
+        aux = np.zeros((5, ny, nx))   # f_l^{n-1} = 0: no mass source
+        o.set_state(pops, aux).step(1)
+        f = o.fields()
+        assert f["fs"].min() == 1.0 and np.abs(f["mdot"]).max() == 0.0
+        assert np.allclose(f["ux"], u0[0] / 2, atol=1e-15)
+        assert np.allclose(f["uy"], u0[1] / 2, atol=1e-15)
+        cx, cy, _, _ = oracle_mod.lattice()
+        post = o.get_state()[0][18:27]
+        assert np.abs(np.tensordot(cx, post, 1)).max() < 1e-14
+        assert np.abs(np.tensordot(cy, post, 1)).max() < 1e-14
+
+
+def test_mass_source_integral_telescopes_in_bulk_liquid(oracle_mod):
+    """With R6's mass source, mdot^n = (1 - rho_s/rho_l) chi (f_l^{n-1} - f_l^n)
+    (Eq. 19), and chi = 1 wherever the order parameter stays near 1, so the
+    sum over steps telescopes: in a box of liquid frozen from a cold wall,
+    sum_n sum_x mdot = (1 - rho_s/rho_l) sum_x (f_l^0 - f_l^N)
+    = (1 - rho_s/rho_l) sum_x f_s^N, exactly up to rounding."""
+    nx, ny = 40, 4
+    p = inputs.params(nx=nx, ny=ny, periodic_x=0, periodic_y=1, dirichlet_x_lo=1,
+                      rho_ratio_sl=0.9, Ste=0.2)
+    o = oracle_mod.Oracle(p).init(np.ones((ny, nx)), np.zeros((ny, nx)))
+    assert o.mdot_integral == 0.0
+    o.step(300)
+    f = o.fields()
+    assert f["phi"].min() > 0.9  # chi = 1 everywhere
+    solid = f["fs"].sum()
+    assert solid > 5.0
+    assert o.mdot_integral == pytest.approx((1 - 0.9) * solid, abs=1e-11)
+    assert np.array_equal(o.solid_profile(), f["fs"].sum(axis=0))
