@@ -40,6 +40,8 @@ def parse_args(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--runs", type=int, default=5,
+                    help="timed runs of --steps steps each; the best is reported")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--size", dest="n", type=int, default=1024, help="lattice size of the bubble drop")
     ap.add_argument("--no-e2e", action="store_true")
@@ -213,24 +215,32 @@ def profiled_traffic(workload: str):
 # the oracle (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(n: int, target_s: float, steps=None):
-    """Time the FP64 oracle on the bubble-drop lattice of size n. Returns
-    (MLUPS, steps, seconds, cores)."""
+def host_cores() -> int:
+    """Cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(n: int, target_s: float, threads: int):
+    """Time the FP64 oracle on the bubble-drop lattice of size n with
+    `threads` host threads (OpenMP over rows). Returns (MLUPS, steps,
+    seconds, threads in effect)."""
     import oracle
     from paper_2403_16122_gb300 import inputs
 
+    used = oracle.set_threads(threads)
     p, phi0, T0 = inputs.bubbles_drop(n=n)
     o = oracle.Oracle(p).init(phi0, T0)
     t0 = time.perf_counter()
     o.step(1)
-    t1 = time.perf_counter()
-    per = t1 - t0
-    if steps is None:
-        steps = max(1, int(target_s / max(per, 1e-6)))
+    per = time.perf_counter() - t0
+    steps = max(1, int(target_s / max(per, 1e-6)))
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
-    return n * n * steps / dt / 1e6, steps, dt, 1
+    return n * n * steps / dt / 1e6, steps, dt, used
 
 
 def run_reference(args, dist: Dist):
@@ -241,6 +251,7 @@ def run_reference(args, dist: Dist):
     from paper_2403_16122_gb300 import inputs
 
     oracle.build()
+    cores = oracle.set_threads(host_cores())
     n = args.n
     p, phi0, T0 = inputs.bubbles_drop(n=n)
     o = oracle.Oracle(p).init(phi0, T0)
@@ -257,14 +268,15 @@ def run_reference(args, dist: Dist):
     o.step(args.steps)
     dt = time.perf_counter() - t0
     value = n * n * args.steps / dt / 1e6
-    sample = f"{args.steps} oracle steps of the bubble drop at {n}x{n} (FP64, one core)"
+    sample = (f"{args.steps} oracle steps of the bubble drop at {n}x{n} (FP64, OpenMP over rows, "
+              f"{cores} threads)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "sample_n": n},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -312,19 +324,25 @@ def run_ours(args, dist: Dist):
     dist.barrier()
     torch.cuda.synchronize()
 
+    # the timed region: exactly K steps (one lbm_step(K) call: K - 1 plain
+    # steps and the observable step that ends every call), run `runs` times
+    # back to back; the best run is reported, every run is listed
     launches0 = lat.launch_count
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
+    runs_ms = []
     with ClockSampler(torch.cuda.current_device()) as clocks:
-        start.record(stream)
-        lat.step(args.steps)
-        end.record(stream)
-        end.synchronize()
+        for _ in range(args.runs):
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            lat.step(args.steps)
+            end.record(stream)
+            end.synchronize()
+            runs_ms.append(start.elapsed_time(end))
     torch.cuda.synchronize()
     dist.barrier()
     torch.cuda.synchronize()
-    ms = start.elapsed_time(end)
-    launches = lat.launch_count - launches0
+    ms = min(runs_ms)
+    launches = (lat.launch_count - launches0) // args.runs
     obs = lat.observables(check=False)
 
     value, ms_max = aggregate(sites * args.steps, ms, dist)
@@ -384,14 +402,7 @@ def run_ours(args, dist: Dist):
         if not args.no_autotune:
             lat16.autotune(steps=args.tune_steps)
         k16 = max(1, min(args.steps, 3000))
-        torch.cuda.synchronize()
-        s16 = torch.cuda.Event(enable_timing=True)
-        e16 = torch.cuda.Event(enable_timing=True)
-        s16.record(lat16.stream)
-        lat16.step(k16)
-        e16.record(lat16.stream)
-        e16.synchronize()
-        ms16 = s16.elapsed_time(e16) / k16
+        ms16 = _timed_steps(lat16, k16, runs=args.runs)
         ob16 = lat16.observables(check=False)
         forms["fp16_storage"] = {
             "value": sites / (ms16 * 1e-3) / 1e6, "unit": "MLUPS", "steps": k16,
@@ -411,7 +422,7 @@ def run_ours(args, dist: Dist):
         if not args.no_autotune:
             latb.autotune(steps=args.tune_steps)
         kb = max(1, min(args.steps, 3000))
-        msb = _timed_steps(latb, kb)
+        msb = _timed_steps(latb, kb, runs=args.runs)
         forms["bf16_storage"] = {
             "value": sites / (msb * 1e-3) / 1e6, "unit": "MLUPS", "steps": kb, "ms_per_step": msb,
             "bytes_per_lu": BYTES_PER_LU_FP16,
@@ -461,14 +472,19 @@ def run_ours(args, dist: Dist):
         import oracle
 
         oracle.build()
-        rate, st, sec, cores = oracle_rate(n, args.cpu_seconds)
+        rate, st, sec, cores = oracle_rate(n, args.cpu_seconds, host_cores())
+        rate1, st1, sec1, _ = oracle_rate(n, args.cpu_seconds / 3, 1)
         cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{st} FP64 oracle steps of the {n}x{n} bubble drop ({sec:.1f} s, one core)"}
+               "sample": f"{st} FP64 oracle steps of the {n}x{n} bubble drop ({sec:.1f} s, "
+                         f"OpenMP over rows on {cores} threads)",
+               "single_core": {"value": rate1, "unit": "MLUPS", "cores": 1,
+                               "sample": f"{st1} steps ({sec1:.1f} s, one thread)"}}
 
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "runs_ms_per_step": [t / args.steps for t in runs_ms],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "nx": n, "ny": n, "sites": sites,
@@ -491,18 +507,23 @@ def run_ours(args, dist: Dist):
     return 0
 
 
-def _timed_steps(lat, k):
-    """Mean ms per step of k steps of handle `lat`, CUDA events on its stream."""
+def _timed_steps(lat, k, runs=1):
+    """Mean ms per step of k steps of handle `lat` (one lbm_step(k) call),
+    CUDA events on its stream; the best of `runs` such calls."""
     import torch
 
     torch.cuda.synchronize()
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record(lat.stream)
-    lat.step(k)
-    e.record(lat.stream)
-    e.synchronize()
-    return s.elapsed_time(e) / k
+    best = None
+    for _ in range(runs):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(lat.stream)
+        lat.step(k)
+        e.record(lat.stream)
+        e.synchronize()
+        t = s.elapsed_time(e) / k
+        best = t if best is None else min(best, t)
+    return best
 
 
 def _batch_handle(cases, storage, dev, exec_mode, chunk, tune_steps):

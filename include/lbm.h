@@ -51,7 +51,8 @@ extern "C" {
 #define LBM_ENOMEM     -2  /* workspace smaller than lbm_workspace_size      */
 #define LBM_ECUDA      -3  /* a CUDA call failed (launch, copy or fault)      */
 #define LBM_ETIMEOUT   -4  /* a device-side wait gave up (batched launches)  */
-#define LBM_EUNSTABLE  -5  /* non-finite fields found by the last reduction  */
+#define LBM_EUNSTABLE  -5  /* non-finite fields or |u| > 0.5 at the last     */
+                           /* observable step                              */
 #define LBM_ESTATE     -6  /* call out of order (e.g. step before init)      */
 #define LBM_ETOOLARGE  -7  /* lattice exceeds the fixed scratch of           */
                            /* lbm_step_noalloc                               */
@@ -133,6 +134,29 @@ typedef struct lbm_params {
 #define LBM_OBS_NONFINITE      10   /* sites with a non-finite field       */
 #define LBM_OBS_COUNT          11
 
+/* Freezing record of an instance (lbm_freezing): quantities that span the
+   whole run since lbm_init_fields rather than one step.
+   LBM_FRZ_STEP           step index of the last observable step (the last
+                          step of the latest lbm_step call).
+   LBM_FRZ_MDOT_INTEGRAL  the mass-source integral: sum over every step since
+                          lbm_init_fields (or lbm_set_state) and every site of
+                          mdot (Eq. 19), accumulated in FP64 on the device as
+                          the steps run (each step's per-tile or per-strip sum
+                          is FP32).
+   LBM_FRZ_FREEZE_STEP    the first observable step at which the solidified
+                          fraction X = sum f_s / sum phi reached
+                          LBM_FREEZE_FRACTION (the freezing time of Sections
+                          4.2-4.3, observed at the observable steps only, so
+                          its resolution is the caller's lbm_step length);
+                          -1 while not reached.
+   LBM_FRZ_SOLID_FRACTION X at the last observable step. */
+#define LBM_FRZ_STEP            0
+#define LBM_FRZ_MDOT_INTEGRAL   1
+#define LBM_FRZ_FREEZE_STEP     2
+#define LBM_FRZ_SOLID_FRACTION  3
+#define LBM_FRZ_COUNT           4
+#define LBM_FREEZE_FRACTION     0.99
+
 typedef struct lbm_handle lbm_handle;
 
 /* Device workspace (bytes) that lbm_create needs for n_inst lattices with
@@ -169,11 +193,27 @@ int lbm_step(lbm_handle* h, int64_t n);
 
 /* Copy the observables record (LBM_OBS_COUNT doubles) of instance `inst`
    from the last step to out. Synchronises the stream. Returns LBM_EUNSTABLE
-   (with the record filled) when any field was non-finite. */
+   (with the record filled) when any field was non-finite or the largest
+   speed exceeded 0.5 lattice units (the scheme's low-Mach expansion of
+   Eqs. 24, 28 and 31 has long broken down there). */
 int lbm_observables(lbm_handle* h, int32_t inst, double* out);
 
+/* Freezing record (LBM_FRZ_COUNT doubles, indices LBM_FRZ_*) of instance
+   `inst` as of the last observable step. Synchronises the stream.
+   LBM_ESTATE before the first lbm_step of a run. */
+int lbm_freezing(lbm_handle* h, int32_t inst, double* out);
+
+/* Solid height profile of instance `inst` at the last observable step:
+   out[x] = sum over y of f_s at column x (nx doubles), the frozen shape of
+   Section 4.2 seen from the cold wall below (with a wall in y). Each
+   column's sum is FP32 over the rows of one tile or strip item, those sums
+   added in FP64. Synchronises the stream. LBM_ESTATE before the first
+   lbm_step of a run. */
+int lbm_solid_profile(lbm_handle* h, int32_t inst, double* out);
+
 /* Observables of every instance: out holds n_inst * LBM_OBS_COUNT doubles.
-   Synchronises the stream. */
+   Synchronises the stream. LBM_EUNSTABLE (records filled) as
+   lbm_observables, for any instance. */
 int lbm_observables_all(lbm_handle* h, double* out);
 
 /* Read back instance `inst`: pops (27*nx*ny doubles) and aux (5*nx*ny
@@ -190,8 +230,10 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux);
 int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
                   const double* aux);
 
-/* Kernel layouts for lbm_step. Both compute the same arithmetic in the same
-   order, so they give bit-identical results.
+/* Kernel layouts for lbm_step. All of them evaluate the same expressions in
+   the same order, but the compiler contracts multiply-adds differently in
+   each kernel, so their results agree to FP32 rounding (about 1e-6 after 60
+   steps), not bit for bit.
    LBM_KERNEL_TILE:  one CTA per tile of a x b sites with a shared-memory
                      halo; handles every wall combination. (a, b) in
                      {(32,8), (32,4), (64,4), (32,16)}; c ignored.
@@ -302,14 +344,18 @@ int64_t lbm_launch_count(const lbm_handle* h);
    cudaMalloc, cudaFree or other allocating routine.
 
    Buffers (device, caller-owned, FP32, 16-byte aligned), in the library's
-   grouped state layout with site = y * pitch + x (pitch >= nx) and
-   plane = pitch * ny: pops_in/pops_out hold 24 * plane floats, the pair
-   (g_i, h_i) of direction i = 1..8 at 2 (i - 1) plane + 2 site and f_i at
-   (15 + i) plane + site; aux_in/aux_out hold 8 * plane floats, the group
-   (g_0, h_0 - L f_l, f_0, f_l) at 4 site and ((phi u)_x, (phi u)_y, p, S) at
-   4 plane + 4 site (L = Cp (T_m - T_w) / Ste). This is exactly the layout of
-   a handle's FP32 state buffers. in and out must not overlap. d_obs receives
-   LBM_OBS_COUNT doubles (device memory).
+   blocked state layout: sites are numbered site = y * pitch + x with pitch a
+   multiple of 32 and >= nx, i.e. site = 32 blk + l (blk = site / 32 the row
+   block, l = x % 32), plane = pitch * ny. pops_in/pops_out hold 24 * plane
+   floats, 768 per block: the pair (g_i, h_i) of direction i = 1..8 at
+   768 blk + 64 (i - 1) + 2 l and f_i at 768 blk + 512 + 32 (i - 1) + l;
+   aux_in/aux_out hold 10 * plane floats, 320 per block: the group
+   (g_0, h_0 - L f_l, f_0, f_l) at 320 blk + 4 l and ((phi u)_x, (phi u)_y,
+   p, S) at 320 blk + 128 + 4 l (the last 64 floats of a block are not used;
+   L = Cp (T_m - T_w) / Ste). This is exactly the layout of a handle's FP32
+   state buffers. An output buffer may share no byte with any of the other
+   three (LBM_EINVAL otherwise). d_obs receives LBM_OBS_COUNT doubles
+   (device memory).
 
    Scratch: the per-tile partial sums of the observables live in one array of
    LBM_NOALLOC_MAX_TILES * LBM_OBS_COUNT doubles (720 KiB) that is part of the
@@ -323,9 +369,13 @@ int64_t lbm_launch_count(const lbm_handle* h);
 
    Device: the current device of the calling thread. On the first call for a
    device the library looks up the array's device address (no allocation)
-   and caches it; make that first call before any stream capture begins.
-   Works for every wall combination (tile kernel). Returns LBM_EINVAL for bad
-   parameters, pointers or pitch, LBM_ECUDA for launch errors. */
+   and caches it for the life of the process; make that first call before
+   any stream capture begins. The cached address does not survive the
+   destruction of the device's context (cudaDeviceReset, or a primary
+   context released and retained again): do not call this entry point after
+   that. Works for every wall combination (tile kernel). Returns LBM_EINVAL
+   for bad parameters, pointers, pitch or overlapping buffers, LBM_ECUDA for
+   launch errors. */
 #define LBM_NOALLOC_MAX_TILES 8192
 int lbm_step_noalloc(const lbm_params* p, const float* pops_in, const float* aux_in,
                      float* pops_out, float* aux_out, int32_t pitch, double* d_obs,

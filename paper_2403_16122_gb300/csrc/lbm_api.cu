@@ -64,8 +64,9 @@ using lbmk::aux_at;
 using lbmk::own0_at;
 using lbmk::pop_at;
 // own-site region, floats per site: (g_0, h_0, f_0, f_l), ((phi u)_x,
-// (phi u)_y, p, S), and for FP16 storage (phi_ref, T_ref)
-int aux_planes(int storage) { return storage == LBM_STORE_FP32 ? 8 : 10; }
+// (phi u)_y, p, S) and (phi_ref, T_ref), the last used by 16-bit storage only
+// (every storage keeps the same block size, lbmk::kAuxBlock)
+int aux_planes(int /*storage*/) { return lbmk::kAuxBlock / 32; }
 
 // D2Q9 directions and weights of the host-side state conversion (Eqs. 22-23)
 const int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -86,6 +87,8 @@ size_t dest_site(const lbm_params& p, int x, int y, int i) {
 
 struct Layout {
     uint64_t inst_off, tile_off, item_off, part_off, obs_off, stage_off, sync_off;
+    uint64_t macc_off, frz_off, prof_off, prof_bytes;
+    std::vector<uint64_t> prof_at;  // doubles from prof_off to each lattice's profile
     std::vector<uint64_t> pop_off[2], aux_off[2];
     uint64_t total;
     int max_tiles, max_items, max_parts, max_sites;
@@ -120,6 +123,14 @@ Layout make_layout(const lbm_params* p, int n, int storage) {
     L.obs_off = off;  off = align_up(off + sizeof(double) * lbmk::kObs * (uint64_t)n);
     L.stage_off = off; off = align_up(off + sizeof(double) * 2 * (uint64_t)L.max_sites);
     L.sync_off = off; off = align_up(off + sizeof(SyncBlock));
+    // running mdot sums (one per partial slot), freezing records, column profiles
+    L.macc_off = off; off = align_up(off + sizeof(double) * (uint64_t)L.max_parts);
+    L.frz_off = off;  off = align_up(off + sizeof(double) * lbmk::kFrz * (uint64_t)n);
+    L.prof_at.resize(n);
+    uint64_t prof_n = 0;
+    for (int k = 0; k < n; ++k) { L.prof_at[k] = prof_n; prof_n += (uint64_t)p[k].nx; }
+    L.prof_bytes = sizeof(double) * prof_n;
+    L.prof_off = off; off = align_up(off + L.prof_bytes);
     for (int b = 0; b < 2; ++b) {
         L.pop_off[b].resize(n);
         L.aux_off[b].resize(n);
@@ -158,6 +169,14 @@ struct lbm_handle {
     double* d_obs = nullptr;
     double* h_obs = nullptr;   // pinned host mirror of d_obs (null: copy to the caller directly)
     double* d_stage = nullptr;
+    double* d_macc = nullptr;  // running mdot sum per partial slot
+    double* d_frz = nullptr;   // freezing records (kFrz doubles per lattice)
+    double* d_prof = nullptr;  // column profiles of f_s (nx doubles per lattice)
+    double* h_frz = nullptr;   // pinned mirror of d_frz
+    std::vector<double> mdot_base;  // mdot summed out of retired slot tables, per lattice
+    std::vector<double> frz_base;   // mdot_base as of the last observable step
+    std::vector<int64_t> step0;     // clock when each lattice was (re)started
+    int64_t clock = 0;              // steps taken by the handle, never reset
     int parity = 0;
     int64_t steps = 0;
     int64_t launches = 0;
@@ -175,6 +194,7 @@ struct lbm_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // `chunk` steps from parity 0 / 1
     ~lbm_handle() {
         if (h_obs) cudaFreeHost(h_obs);
+        if (h_frz) cudaFreeHost(h_frz);
     }
 };
 
@@ -191,6 +211,8 @@ void fill_inst(lbm_handle* h, int k) {
     double L = 0.0;
     lbmk::inst_from_params(p, &I, &L);
     I.part_stride = h->layout.max_parts;
+    I.macc = h->d_macc;
+    I.prof = h->d_prof + h->layout.prof_at[k];
     for (int b = 0; b < 2; ++b) {
         I.pop[b] = h->ws + h->layout.pop_off[b][k];
         I.aux[b] = reinterpret_cast<float*>(h->ws + h->layout.aux_off[b][k]);
@@ -268,8 +290,54 @@ void drop_graphs(lbm_handle* h) {
     }
 }
 
+// The running mdot sums live in the slots of the current tile or item table;
+// before the table is rebuilt they are summed per lattice (in slot order, in
+// FP64) into mdot_base and the slots are cleared.
+int fold_mdot(lbm_handle* h) {
+    if (!h->initialised) return LBM_OK;
+    int n_parts = 0;
+    for (int k = 0; k < h->n_inst; ++k) n_parts = std::max(n_parts, h->inst[k].part_end);
+    if (n_parts <= 0) return LBM_OK;
+    std::vector<double> v((size_t)n_parts);
+    cudaError_t e = cudaMemcpyAsync(v.data(), h->d_macc, v.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_macc, 0, v.size() * sizeof(double), h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int k = 0; k < h->n_inst; ++k) {
+        double sum = 0.0;
+        for (int q = h->inst[k].part_begin; q < h->inst[k].part_end; ++q) sum += v[(size_t)q];
+        h->mdot_base[k] += sum;
+    }
+    return LBM_OK;
+}
+
+// A lattice starts a new run (lbm_init_fields, lbm_set_state): its running
+// mdot sums, profile and freezing record restart.
+int restart_records(lbm_handle* h, int k) {
+    const Inst& I = h->inst[k];
+    cudaError_t e = cudaSuccess;
+    if (I.part_end > I.part_begin)
+        e = cudaMemsetAsync(h->d_macc + I.part_begin, 0,
+                            sizeof(double) * (size_t)(I.part_end - I.part_begin), h->stream);
+    const double rec[lbmk::kFrz] = {0.0, 0.0, -1.0, 0.0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_frz + (size_t)k * lbmk::kFrz, rec, sizeof(rec),
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // rec is on this stack
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->mdot_base[k] = 0.0;
+    h->frz_base[k] = 0.0;
+    h->step0[k] = h->clock;
+    return LBM_OK;
+}
+
 int upload_tables(lbm_handle* h) {
     drop_graphs(h);  // captured launches carry the old item counts
+    {
+        const int rc = fold_mdot(h);
+        if (rc != LBM_OK) return rc;
+    }
     if (h->kind == LBM_KERNEL_STAGED) {
         cudaError_t e = lbmk::prepare_staged(h->warps, h->regs, h->storage);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -364,6 +432,13 @@ cudaError_t sync_checked(lbm_handle* h) {
     return cudaSuccess;
 }
 
+// A record reports an unstable step: a non-finite field, or a speed above
+// 0.5 (NaN compares false, so a NaN maximum is caught by the count).
+constexpr double kMaxSpeed = 0.5;
+bool unstable(const double* rec) {
+    return rec[LBM_OBS_NONFINITE] > 0 || rec[LBM_OBS_UMAX] > kMaxSpeed;
+}
+
 // n doubles of the observable records from offset off to the caller's out,
 // through the pinned mirror (the driver stages a copy into pageable memory
 // with an extra synchronisation), then the synchronising check.
@@ -419,11 +494,22 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
     h->d_obs = reinterpret_cast<double*>(h->ws + h->layout.obs_off);
     h->d_stage = reinterpret_cast<double*>(h->ws + h->layout.stage_off);
     h->d_sync = reinterpret_cast<SyncBlock*>(h->ws + h->layout.sync_off);
+    h->d_macc = reinterpret_cast<double*>(h->ws + h->layout.macc_off);
+    h->d_frz = reinterpret_cast<double*>(h->ws + h->layout.frz_off);
+    h->d_prof = reinterpret_cast<double*>(h->ws + h->layout.prof_off);
+    h->mdot_base.assign(n_inst, 0.0);
+    h->frz_base.assign(n_inst, 0.0);
+    h->step0.assign(n_inst, 0);
+    if (cudaMallocHost(&h->h_frz, sizeof(double) * lbmk::kFrz * n_inst) != cudaSuccess) {
+        h->h_frz = nullptr;  // the records are then copied to the caller's memory directly
+        cudaGetLastError();
+    }
     if (cudaMallocHost(&h->h_obs, sizeof(double) * lbmk::kObs * n_inst) != cudaSuccess) {
         h->h_obs = nullptr;  // the observables are then copied to the caller's memory directly
         cudaGetLastError();
     }
-    if (cudaMemsetAsync(h->d_sync, 0, sizeof(SyncBlock), h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->d_sync, 0, sizeof(SyncBlock), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->d_macc, 0, h->layout.frz_off - h->layout.macc_off, h->stream) != cudaSuccess) {
         delete h;
         return LBM_ECUDA;
     }
@@ -471,6 +557,10 @@ int lbm_init_fields(lbm_handle* h, int32_t inst, const double* phi0, const doubl
     h->initialised = true;
     h->have_obs = false;
     if (inst == 0) h->steps = 0;
+    {
+        const int rc = restart_records(h, inst);
+        if (rc != LBM_OK) return rc;
+    }
     if (h->failed) {  // a fresh state clears an expired barrier wait
         e = cudaMemsetAsync(&h->d_sync->err, 0, sizeof(int), h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -484,6 +574,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
     if (!h || n < 0) return LBM_EINVAL;
     if (!h->initialised) return LBM_ESTATE;
     if (h->failed) return LBM_ETIMEOUT;
+    h->clock += n;
     // every step but the last runs without observables, in the handle's form
     int64_t body = n > 0 ? n - 1 : 0;
     if (h->exec != LBM_EXEC_LAUNCH) {
@@ -513,6 +604,10 @@ int lbm_step(lbm_handle* h, int64_t n) {
     }
     for (int64_t k = 0; k < body + (n > 0 ? 1 : 0); ++k) {
         const int obs = (k == body);
+        if (obs) {  // the observable step adds each column's f_s to a zeroed profile
+            cudaError_t e = cudaMemsetAsync(h->d_prof, 0, h->layout.prof_bytes, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
         cudaError_t e = enqueue_step(h, h->parity, obs, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
@@ -520,10 +615,12 @@ int lbm_step(lbm_handle* h, int64_t n) {
         h->steps++;
     }
     if (n > 0) {
-        cudaError_t e = lbmk::launch_reduce_obs(h->d_inst, h->n_inst, h->d_part, h->d_obs, h->stream);
+        cudaError_t e = lbmk::launch_reduce_obs(h->d_inst, h->n_inst, h->d_part, h->d_obs, h->d_frz,
+                                                h->clock, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
         h->have_obs = true;
+        h->frz_base = h->mdot_base;
     }
     return LBM_OK;
 }
@@ -535,8 +632,37 @@ int lbm_observables_all(lbm_handle* h, double* out) {
     if (e != cudaSuccess) return cuda_fail(e);
     if (h->failed) return LBM_ETIMEOUT;
     for (int k = 0; k < h->n_inst; ++k)
-        if (out[k * lbmk::kObs + LBM_OBS_NONFINITE] > 0) return LBM_EUNSTABLE;
+        if (unstable(out + (size_t)k * lbmk::kObs)) return LBM_EUNSTABLE;
     return LBM_OK;
+}
+
+int lbm_freezing(lbm_handle* h, int32_t inst, double* out) {
+    if (!inst_ok(h, inst) || !out) return LBM_EINVAL;
+    if (!h->have_obs) return LBM_ESTATE;
+    double* dst = h->h_frz ? h->h_frz + (size_t)inst * lbmk::kFrz : out;
+    cudaError_t e = cudaMemcpyAsync(dst, h->d_frz + (size_t)inst * lbmk::kFrz,
+                                    sizeof(double) * lbmk::kFrz, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = sync_checked(h);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (h->h_frz) memcpy(out, dst, sizeof(double) * lbmk::kFrz);
+    // steps count from this lattice's own start; slot sums retired by a table
+    // rebuild before the record was taken are added back
+    const double s0 = (double)h->step0[inst];
+    out[LBM_FRZ_STEP] -= s0;
+    if (out[LBM_FRZ_FREEZE_STEP] >= 0.0) out[LBM_FRZ_FREEZE_STEP] -= s0;
+    out[LBM_FRZ_MDOT_INTEGRAL] += h->frz_base[inst];
+    return h->failed ? LBM_ETIMEOUT : LBM_OK;
+}
+
+int lbm_solid_profile(lbm_handle* h, int32_t inst, double* out) {
+    if (!inst_ok(h, inst) || !out) return LBM_EINVAL;
+    if (!h->have_obs) return LBM_ESTATE;
+    cudaError_t e = cudaMemcpyAsync(out, h->d_prof + h->layout.prof_at[inst],
+                                    sizeof(double) * (size_t)h->params[inst].nx,
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = sync_checked(h);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return h->failed ? LBM_ETIMEOUT : LBM_OK;
 }
 
 int lbm_observables(lbm_handle* h, int32_t inst, double* out) {
@@ -545,7 +671,7 @@ int lbm_observables(lbm_handle* h, int32_t inst, double* out) {
     cudaError_t e = read_obs(h, (size_t)inst * lbmk::kObs, lbmk::kObs, out);
     if (e != cudaSuccess) return cuda_fail(e);
     if (h->failed) return LBM_ETIMEOUT;
-    return out[LBM_OBS_NONFINITE] > 0 ? LBM_EUNSTABLE : LBM_OK;
+    return unstable(out) ? LBM_EUNSTABLE : LBM_OK;
 }
 
 namespace {
@@ -581,8 +707,8 @@ int download_planar(lbm_handle* h, int32_t inst, std::vector<T>& tp, std::vector
             const size_t k = (size_t)y * p.nx + x;
             const int site = y * I.pitch + x;
             for (int set = 0; set < 3; ++set)
-                for (int i = 1; i < 9; ++i) tp[(9 * set + i) * n + k] = rp[pop_at(set, i, plane, site)];
-            for (int a = 0; a < na; ++a) ta[a * n + k] = ra[aux_at(a, plane, site)];
+                for (int i = 1; i < 9; ++i) tp[(9 * set + i) * n + k] = rp[pop_at(set, i, site)];
+            for (int a = 0; a < na; ++a) ta[a * n + k] = ra[aux_at(a, site)];
             if (!half)
                 for (int set = 0; set < 3; ++set) tp[9 * set * n + k] = T(ra[own0_at(site, set)]);
         }
@@ -604,8 +730,8 @@ int upload_planar(lbm_handle* h, int32_t inst, const std::vector<T>& tp, const s
             const size_t k = (size_t)y * p.nx + x;
             const int site = y * I.pitch + x;
             for (int set = 0; set < 3; ++set)
-                for (int i = 1; i < 9; ++i) rp[pop_at(set, i, plane, site)] = tp[(9 * set + i) * n + k];
-            for (int a = 0; a < na; ++a) ra[aux_at(a, plane, site)] = ta[a * n + k];
+                for (int i = 1; i < 9; ++i) rp[pop_at(set, i, site)] = tp[(9 * set + i) * n + k];
+            for (int a = 0; a < na; ++a) ra[aux_at(a, site)] = ta[a * n + k];
             if (!half)
                 for (int set = 0; set < 3; ++set) ra[own0_at(site, set)] = (float)tp[9 * set * n + k];
         }
@@ -732,10 +858,22 @@ int lbm_get_state(lbm_handle* h, int32_t inst, double* pops, double* aux) {
     return LBM_OK;
 }
 
+namespace {
+int set_state_fp32(lbm_handle* h, int32_t inst, const double* pops, const double* aux);
+}
+
 int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
     if (!inst_ok(h, inst) || !pops || !aux) return LBM_EINVAL;
-    if (h->storage == LBM_STORE_FP16) return set_state_16<__half>(h, inst, pops, aux);
-    if (h->storage == LBM_STORE_BF16) return set_state_16<__nv_bfloat16>(h, inst, pops, aux);
+    int rc;
+    if (h->storage == LBM_STORE_FP16) rc = set_state_16<__half>(h, inst, pops, aux);
+    else if (h->storage == LBM_STORE_BF16) rc = set_state_16<__nv_bfloat16>(h, inst, pops, aux);
+    else rc = set_state_fp32(h, inst, pops, aux);
+    if (rc != LBM_OK) return rc;
+    return restart_records(h, inst);  // a new run: the freezing record restarts
+}
+
+namespace {
+int set_state_fp32(lbm_handle* h, int32_t inst, const double* pops, const double* aux) {
     const lbm_params& p = h->params[inst];
     const Inst& I = h->inst[inst];
     const size_t n = (size_t)p.nx * p.ny;
@@ -750,6 +888,7 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops, const double*
     h->have_obs = false;
     return LBM_OK;
 }
+}  // namespace
 
 int lbm_set_thermal_walls(lbm_handle* h, int32_t inst, int32_t x_lo, int32_t x_hi,
                           int32_t y_lo, int32_t y_hi) {

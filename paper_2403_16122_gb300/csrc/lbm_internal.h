@@ -12,6 +12,8 @@
 namespace lbmk {
 
 constexpr int kObs = 11;  // observables per instance (LBM_OBS_COUNT)
+constexpr int kFrz = LBM_FRZ_COUNT;       // doubles of a lattice's freezing record
+constexpr double kFreezeFraction = LBM_FREEZE_FRACTION;
 
 // Bits of Inst::flags.
 enum : int {
@@ -26,20 +28,27 @@ enum : int {
     kPhaseProps = 1 << 8,  // per-phase heat capacity / conductivity
 };
 
-// Grouped state layout of one ping-pong buffer of a lattice. Sites are
-// numbered site = y * pitch + x, and plane = pitch * ny. Values that a site
-// pulls from the same neighbour, or keeps for itself, sit side by side, so
-// that one wide copy moves them:
-//   population region (elements of the storage type, FP32 or FP16):
-//     (g_i, h_i) of direction i = 1..8 at 2 (i - 1) plane + 2 site + set,
-//     f_i at (15 + i) plane + site                 -> 24 elements per site;
-//   own-site region (FP32):
-//     (g_0, h_0 - L f_l, f_0, f_l) at 4 site,
-//     ((phi u)_x, (phi u)_y, p, S) at 4 plane + 4 site,
-//     FP16 storage only: (phi_ref, T_ref) at 8 plane + 2 site.
+// Blocked state layout of one ping-pong buffer of a lattice. Sites are
+// numbered site = y * pitch + x with pitch a multiple of 32, so that
+// site = 32 * blk + l with blk = y * (pitch / 32) + x / 32 the row block of 32
+// sites and l = x % 32 the site's place in it. Every block keeps all the
+// values of its 32 sites together (one contiguous run per block, blocks in
+// row order), so the values of a row segment share DRAM pages instead of
+// lying in 24 or more planes a whole lattice apart. Inside a block, values a
+// site pulls from the same neighbour, or keeps for itself, sit side by side,
+// so that one wide copy moves them:
+//   population region (kPopBlock elements of the storage type per block):
+//     (g_i, h_i) of direction i = 1..8 at 64 (i - 1) + 2 l + set,
+//     f_i at 512 + 32 (i - 1) + l                   -> 24 elements per site;
+//   own-site region (kAuxBlock FP32 values per block):
+//     (g_0, h_0 - L f_l, f_0, f_l) at 4 l,
+//     ((phi u)_x, (phi u)_y, p, S) at 128 + 4 l,
+//     16-bit storage only: (phi_ref, T_ref) at 256 + 2 l.
 // h_0 is stored shifted by -L f_l of the same site and step, which keeps every
 // stored value O(1) (the latent part of H is carried by f_l instead).
 constexpr int kPopElems = 24;
+constexpr int kPopBlock = kPopElems * 32;  // population elements per block
+constexpr int kAuxBlock = 10 * 32;         // own-site floats per block
 
 // The two 16-bit storage types (FP16: 10-bit mantissa, BF16: 7-bit mantissa
 // and the FP32 exponent range) behind one set of conversions.
@@ -76,23 +85,31 @@ struct Bits16<__nv_bfloat16> {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
     }
 };
-__host__ __device__ inline int gh_at(int i, int plane, int site, int set) {
-    return 2 * (i - 1) * plane + 2 * site + set;
+__host__ __device__ inline int gh_at(int i, int site, int set) {
+    return (site >> 5) * kPopBlock + 64 * (i - 1) + 2 * (site & 31) + set;
 }
-__host__ __device__ inline int f_at(int i, int plane, int site) { return (15 + i) * plane + site; }
-__host__ __device__ inline int own0_at(int site, int c) { return 4 * site + c; }
-__host__ __device__ inline int own1_at(int plane, int site, int c) { return 4 * plane + 4 * site + c; }
-__host__ __device__ inline int ref_at(int plane, int site, int c) { return 8 * plane + 2 * site + c; }
+__host__ __device__ inline int f_at(int i, int site) {
+    return (site >> 5) * kPopBlock + 512 + 32 * (i - 1) + (site & 31);
+}
+__host__ __device__ inline int own0_at(int site, int c) {
+    return (site >> 5) * kAuxBlock + 4 * (site & 31) + c;
+}
+__host__ __device__ inline int own1_at(int site, int c) {
+    return (site >> 5) * kAuxBlock + 128 + 4 * (site & 31) + c;
+}
+__host__ __device__ inline int ref_at(int site, int c) {
+    return (site >> 5) * kAuxBlock + 256 + 2 * (site & 31) + c;
+}
 // Element offset of population (set, i) in the population region (i >= 1).
-__host__ __device__ inline int pop_at(int set, int i, int plane, int site) {
-    return set < 2 ? gh_at(i, plane, site, set) : f_at(i, plane, site);
+__host__ __device__ inline int pop_at(int set, int i, int site) {
+    return set < 2 ? gh_at(i, site, set) : f_at(i, site);
 }
 // Carried field k of the own-site region: 0 f_l, 1 (phi u)_x, 2 (phi u)_y,
 // 3 p, 4 S, 5 phi_ref, 6 T_ref, 7/8/9 the rest populations g_0, h_0, f_0.
-__host__ __device__ inline int aux_at(int k, int plane, int site) {
+__host__ __device__ inline int aux_at(int k, int site) {
     return k == 0 ? own0_at(site, 3)
-                  : (k <= 4 ? own1_at(plane, site, k - 1)
-                            : (k <= 6 ? ref_at(plane, site, k - 5) : own0_at(site, k - 7)));
+                  : (k <= 4 ? own1_at(site, k - 1)
+                            : (k <= 6 ? ref_at(site, k - 5) : own0_at(site, k - 7)));
 }
 
 // One lattice as the kernels see it (state in the grouped layout above).
@@ -103,6 +120,10 @@ struct Inst {
     float* aux[2];            // own-site regions
     int part_begin, part_end; // observable partials of this lattice's tiles
     int part_stride;          // partials are observable-major: [kObs][part_stride]
+    double* macc;             // per tile / strip item (index `part`): sum of mdot over
+                              // its sites, accumulated over every step (null: off)
+    double* prof;             // nx doubles: sum over y of f_s per column, added to
+                              // by observable steps (zeroed before each; null: off)
     // physics, single precision
     float L, Hs, Tm, Cp, Cpref, Tw;
     float omega_g, omega_h;          // 1 / tau

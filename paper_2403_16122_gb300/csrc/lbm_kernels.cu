@@ -132,10 +132,10 @@ template <typename ST, bool NC>
 __device__ __forceinline__ float ldPop(const LatT<NC>& l, int set, int i, int idx) {
     if (i == 0) return ld_f32<NC>(l.Aaux + own0_at(idx, set));
     if constexpr (sizeof(ST) == 4) {
-        return ld_f32<NC>(l.A + pop_at(set, i, l.plane, idx));
+        return ld_f32<NC>(l.A + pop_at(set, i, idx));
     } else {
         const unsigned short* A = reinterpret_cast<const unsigned short*>(l.A);
-        return Bits16<ST>::to_f(Bits16<ST>::from_bits(ld_u16<NC>(A + pop_at(set, i, l.plane, idx))));
+        return Bits16<ST>::to_f(Bits16<ST>::from_bits(ld_u16<NC>(A + pop_at(set, i, idx))));
     }
 }
 
@@ -158,7 +158,7 @@ __device__ __forceinline__ float f_rest(int i, float p) {
 }
 template <bool NC>
 __device__ __forceinline__ float ldAux(const LatT<NC>& l, int k, int idx) {
-    return ld_f32<NC>(l.Aaux + aux_at(k, l.plane, idx));
+    return ld_f32<NC>(l.Aaux + aux_at(k, idx));
 }
 
 // Pull of set `set` (0 g, 1 h, 2 f) at lattice site (x, y): v[i] is the
@@ -558,8 +558,8 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
             g0n = gn; h0n = hn; f0n = fn;  // own-site group, stored below
         } else if constexpr (sizeof(ST) == 4) {
             float* B = static_cast<float*>(Bv);
-            *reinterpret_cast<float2*>(B + gh_at(i, plane, own, 0)) = make_float2(gn, hn);
-            B[f_at(i, plane, own)] = fn;
+            *reinterpret_cast<float2*>(B + gh_at(i, own, 0)) = make_float2(gn, hn);
+            B[f_at(i, own)] = fn;
         } else {
             {
                 // deviations from the rest equilibria (g, h: destination's
@@ -572,8 +572,8 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                 const float df = (fn - f_rest(i, pn)) * kFScale;
                 const unsigned qgh = C16::pack2(dg, dh);  // (g_i, h_i) in one word
                 const ST qf = C16::from_f(df);
-                *reinterpret_cast<unsigned*>(B + gh_at(i, plane, own, 0)) = qgh;
-                B[f_at(i, plane, own)] = C16::bits(qf);
+                *reinterpret_cast<unsigned*>(B + gh_at(i, own, 0)) = qgh;
+                B[f_at(i, own)] = C16::bits(qf);
                 const float2 rgh = C16::unpack2(qgh);
                 eg += dg - rgh.x;
                 eh += dh - rgh.y;
@@ -587,9 +587,9 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         f0n += ef * kInvFScale;
     }
     *reinterpret_cast<float4*>(Baux + own0_at(own, 0)) = make_float4(g0n, h0n, f0n, m.fl);
-    *reinterpret_cast<float4*>(Baux + own1_at(plane, own, 0)) = make_float4(phiux, phiuy, pn, S);
+    *reinterpret_cast<float4*>(Baux + own1_at(own, 0)) = make_float4(phiux, phiuy, pn, S);
     if constexpr (sizeof(ST) != 4)  // references of this site for the next step
-        *reinterpret_cast<float2*>(Baux + ref_at(plane, own, 0)) = make_float2(phi, T);
+        *reinterpret_cast<float2*>(Baux + ref_at(own, 0)) = make_float2(phi, T);
 
     if (OBS) {
         ob.add(0, phi);
@@ -813,6 +813,29 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
         for (int j = 0; j < kObs; ++j) v[j] = ob.total(j);
         block_reduce_obs<NT>(v, partials + T.part, I.part_stride);
     }
+    // the tile's mdot of this step joins its FP64 running sum (warp sums,
+    // then the warps in order), and on observable steps each column's f_s
+    // (rows in order) is added to the lattice's column profile
+    __shared__ float s_md[NT / 32];
+    __shared__ float s_col[TY][TX];
+    if (I.macc || (OBS && I.prof)) {
+        float md = active ? m.mdot : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md += __shfl_xor_sync(0xffffffffu, md, o);
+        if ((tid & 31) == 0) s_md[tid >> 5] = md;
+        if (OBS) s_col[ty][tx] = active ? m.fs : 0.f;
+        __syncthreads();
+        if (I.macc && tid == 0) {
+            float sum = 0.f;
+            for (int w = 0; w < NT / 32; ++w) sum += s_md[w];
+            I.macc[T.part] += (double)sum;
+        }
+        if (OBS && I.prof && ty == 0 && tx < tw) {
+            float sum = 0.f;
+            for (int r = 0; r < th; ++r) sum += s_col[r][tx];
+            atomicAdd(I.prof + x0 + tx, (double)sum);
+        }
+    }
 }
 
 template <int TX, int TY, bool OBS>
@@ -933,6 +956,10 @@ template <typename ST>
 __host__ __device__ constexpr int stage_planes() { return sizeof(ST) == 4 ? 32 : 34; }
 template <typename ST>
 __host__ __device__ constexpr int slot_floats() { return stage_planes<ST>() * 32; }
+// Dynamic shared memory of one warp of a staged kernel: STG ring slots, then
+// one float per lane for the running mdot sum of the warp's item.
+template <typename ST, int STG>
+__host__ __device__ constexpr int warp_smem_floats() { return STG * slot_floats<ST>() + 32; }
 
 __device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
@@ -994,8 +1021,8 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, i
     const int own = o0 + xc;
     const unsigned long long pol = l2_policy(hint);
     cp_async_p<16>(slot + 4 * lane, l.Aaux + own0_at(own, 0), pol);
-    cp_async_p<16>(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(plane, own, 0), pol);
-    if constexpr (kHalf) cp_async_p<8>(slot + kSlotR + 2 * lane, l.Aaux + ref_at(plane, own, 0), pol);
+    cp_async_p<16>(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(own, 0), pol);
+    if constexpr (kHalf) cp_async_p<8>(slot + kSlotR + 2 * lane, l.Aaux + ref_at(own, 0), pol);
     const unsigned short* A16 = reinterpret_cast<const unsigned short*>(l.A);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -1008,14 +1035,14 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, i
             // planes and rows hold an even number of 16-bit values, so every
             // aligned word lies inside its row
             cp_async_p<4>(slot + slot_gh(i, lane),
-                          reinterpret_cast<const float*>(A16 + gh_at(si, plane, site, 0)), pol);
+                          reinterpret_cast<const float*>(A16 + gh_at(si, site, 0)), pol);
             if (!macro_only)
                 cp_async_p<4>(slot + slot_f(i, lane),
-                              reinterpret_cast<const float*>(A16 + (f_at(si, plane, site) & ~1)),
+                              reinterpret_cast<const float*>(A16 + (f_at(si, site) & ~1)),
                               pol);
         } else {
-            cp_async_p<8>(slot + slot_gh(i, lane), l.A + gh_at(si, plane, site, 0), pol);
-            if (!macro_only) cp_async_p<4>(slot + slot_f(i, lane), l.A + f_at(si, plane, site), pol);
+            cp_async_p<8>(slot + slot_gh(i, lane), l.A + gh_at(si, site, 0), pol);
+            if (!macro_only) cp_async_p<4>(slot + slot_f(i, lane), l.A + f_at(si, site), pol);
         }
     }
 }
@@ -1208,6 +1235,12 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
 
     RowObs ob;
     if (OBS) ob.zero();
+    // mdot of this lane's sites over the item (every step; the staged kernels
+    // keep it in shared memory after the ring, which spares a register), f_s
+    // of its column over the item's rows (observable steps)
+    float md_acc = 0.f, col_fs = 0.f;
+    auto md_smem = [&]() -> float& { return ring[STG * slot_floats<ST>() + lane]; };
+    if constexpr (STG > 0) md_smem() = 0.f;
 
     // rows y-1 (m), y (0) and y+1 (p) of phi, rho, p^{n-1}, S^{n-1} (and T)
     float phm = 0.f, ph0, php = 0.f, rhm = 0.f, rh0, rhp = 0.f;
@@ -1365,6 +1398,11 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         }
 
         if (OBS) ob.flush(lane);
+        if (out_lane) {
+            if constexpr (STG > 0) md_smem() += mO.mdot;
+            else md_acc += mO.mdot;
+            if (OBS) col_fs += mO.fs;
+        }
 
         // advance the window
         phm = ph0; ph0 = php; rhm = rh0; rh0 = rhp;
@@ -1376,6 +1414,16 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     if constexpr (STG > 0) cp_async_wait<0>();  // the trailing groups are empty
 
     if (OBS && lane < kObs) partials[(long long)lane * I.part_stride + W.part] = ob.total();
+    // the item's mdot of this step joins its FP64 running sum (one warp owns
+    // the item, so the read-modify-write needs no atomic)
+    double* const macc = insts[W.inst].macc;  // read here: no register held over the rows
+    if (macc) {
+        if constexpr (STG > 0) md_acc = md_smem();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md_acc += __shfl_xor_sync(0xffffffffu, md_acc, o);
+        if (lane == 0) macc[W.part] += (double)md_acc;
+    }
+    if (OBS && I.prof && out_lane) atomicAdd(I.prof + c.xc, (double)col_fs);
 }
 
 template <int WARPS, int MINB, bool OBS, typename ST>
@@ -1404,7 +1452,7 @@ step_strip_staged(const Inst* __restrict__ insts, const Item* __restrict__ items
     const int it = blockIdx.x * WARPS + warp;
     if (it >= n_items) return;  // whole warp leaves together; no block barrier in the body
     strip_item<OBS, ST, true, STG>(insts, items[it], parity, partials,
-                                   ring_smem + warp * (STG * slot_floats<ST>()));
+                                   ring_smem + warp * warp_smem_floats<ST, STG>());
 }
 
 // Device-wide barrier between the steps of the persistent kernel. Every CTA
@@ -1462,7 +1510,7 @@ step_strip_persistent(const Inst* __restrict__ insts, const Item* __restrict__ i
                       int n_items, int parity0, int nsteps, unsigned* bar, int* err,
                       unsigned long long limit_ns) {
     extern __shared__ __align__(16) float ring_smem[];
-    float* ring = ring_smem + (threadIdx.x >> 5) * (STG * slot_floats<ST>());
+    float* ring = ring_smem + (threadIdx.x >> 5) * warp_smem_floats<ST, STG>();
     const int warp = blockIdx.x * WARPS + (threadIdx.x >> 5);
     const int stride = gridDim.x * WARPS;
     for (int s = 0; s < nsteps; ++s) {
@@ -1538,13 +1586,13 @@ __global__ void init_fp32(const Inst* __restrict__ insts, int inst, InitConst c,
                 A[own0_at(site, 1)] = (float)hq;
                 A[own0_at(site, 2)] = 0.f;
             } else {
-                P[gh_at(i, plane, site, 0)] = g;
-                P[gh_at(i, plane, site, 1)] = (float)hq;
-                P[f_at(i, plane, site)] = 0.f;
+                P[gh_at(i, site, 0)] = g;
+                P[gh_at(i, site, 1)] = (float)hq;
+                P[f_at(i, site)] = 0.f;
             }
         }
         A[own0_at(site, 3)] = (float)fl;
-        for (int k = 0; k < 4; ++k) A[own1_at(plane, site, k)] = 0.f;
+        for (int k = 0; k < 4; ++k) A[own1_at(site, k)] = 0.f;
     }
 }
 
@@ -1592,15 +1640,15 @@ __global__ void init_16(const Inst* __restrict__ insts, int inst, InitConst c,
                 A[own0_at(idx, 2)] = 0.f;
                 continue;
             }
-            P[gh_at(i, plane, idx, 0)] = Bits16<ST>::from_d(w * ph - (double)(wf * phd));  // Eq. 24, u = 0
-            P[gh_at(i, plane, idx, 1)] =
+            P[gh_at(i, idx, 0)] = Bits16<ST>::from_d(w * ph - (double)(wf * phd));  // Eq. 24, u = 0
+            P[gh_at(i, idx, 1)] =
                 Bits16<ST>::from_d(w * c.Cp * T * (c.Cpref / c.Cp) - (double)(wf * I.Cpref * Td));  // Eq. 28
-            P[f_at(i, plane, idx)] = Bits16<ST>::from_f(0.f);  // Eq. 31 vanishes at p = 0, u = 0
+            P[f_at(i, idx)] = Bits16<ST>::from_f(0.f);  // Eq. 31 vanishes at p = 0, u = 0
         }
         A[own0_at(idx, 3)] = (float)fl;
-        for (int k = 0; k < 4; ++k) A[own1_at(plane, idx, k)] = 0.f;
-        A[ref_at(plane, idx, 0)] = phr;
-        A[ref_at(plane, idx, 1)] = Tr;
+        for (int k = 0; k < 4; ++k) A[own1_at(idx, k)] = 0.f;
+        A[ref_at(idx, 0)] = phr;
+        A[ref_at(idx, 1)] = Tr;
     }
 }
 
@@ -1671,7 +1719,7 @@ cudaError_t launch_strip_w(const Inst* d_inst, const Item* d_items, int n_items,
 // Staged launches: ring depth and dynamic shared memory of a variant.
 template <int WARPS, int MINB, int STG, typename ST>
 struct Staged {
-    static constexpr int kSmem = WARPS * STG * slot_floats<ST>() * (int)sizeof(float);
+    static constexpr int kSmem = WARPS * warp_smem_floats<ST, STG>() * (int)sizeof(float);
     static cudaError_t prepare() {
         cudaError_t e = cudaFuncSetAttribute(step_strip_staged<WARPS, MINB, STG, false, ST>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
@@ -1737,7 +1785,7 @@ int plain_resident_warps() {
 // the co-resident grid for it.
 template <int WARPS, int MINB, int STG, typename ST>
 struct Persist {
-    static constexpr int kSmem = WARPS * STG * slot_floats<ST>() * (int)sizeof(float);
+    static constexpr int kSmem = WARPS * warp_smem_floats<ST, STG>() * (int)sizeof(float);
     static cudaError_t prepare() {
         return cudaFuncSetAttribute(step_strip_persistent<WARPS, MINB, STG, ST>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);

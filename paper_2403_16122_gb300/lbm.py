@@ -27,6 +27,9 @@ OBS_NAMES = (
     "phi_mdot", "solid_col", "solid_row", "umax", "nonfinite",
 )
 LBM_OBS_COUNT = len(OBS_NAMES)
+FRZ_NAMES = ("step", "mdot_integral", "freeze_step", "solid_fraction")
+LBM_FRZ_COUNT = len(FRZ_NAMES)
+LBM_FREEZE_FRACTION = 0.99
 
 
 class lbm_params(ctypes.Structure):
@@ -69,6 +72,7 @@ SYMBOLS = (
     "lbm_step_count", "lbm_launch_count", "lbm_destroy", "lbm_error_string",
     "lbm_set_kernel", "lbm_get_kernel", "lbm_autotune", "lbm_step_noalloc",
     "lbm_set_exec", "lbm_get_exec", "lbm_barrier_selftest", "lbm_set_thermal_walls",
+    "lbm_freezing", "lbm_solid_profile",
 )
 LBM_KERNEL_TILE, LBM_KERNEL_STRIP, LBM_KERNEL_STAGED = 0, 1, 2
 LBM_EXEC_LAUNCH, LBM_EXEC_GRAPH, LBM_EXEC_PERSISTENT = 0, 1, 2
@@ -114,10 +118,13 @@ def load(path: str | None = None):
         lib.lbm_get_exec.argtypes = [vp, P(i32)]
         lib.lbm_barrier_selftest.argtypes = [vp, u64, P(i32)]
         lib.lbm_set_thermal_walls.argtypes = [vp, i32, i32, i32, i32, i32]
+        lib.lbm_freezing.argtypes = [vp, i32, dp]
+        lib.lbm_solid_profile.argtypes = [vp, i32, dp]
         lib.lbm_error_string.argtypes = [ctypes.c_int]
         lib.lbm_error_string.restype = ctypes.c_char_p
         for name in ("lbm_workspace_size", "lbm_create", "lbm_init_fields", "lbm_step",
-                     "lbm_observables", "lbm_observables_all", "lbm_get_state", "lbm_set_state"):
+                     "lbm_observables", "lbm_observables_all", "lbm_get_state", "lbm_set_state",
+                     "lbm_freezing", "lbm_solid_profile"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -188,6 +195,22 @@ def lbm_observables_all(h, n_inst: int, check: bool = True) -> np.ndarray:
     rc = load().lbm_observables_all(h, _dptr(out))
     if rc and (check or rc != LBM_EUNSTABLE):
         raise LbmError(rc, "lbm_observables_all")
+    return out
+
+
+def lbm_freezing(h, inst: int) -> np.ndarray:
+    out = np.zeros(LBM_FRZ_COUNT)
+    rc = load().lbm_freezing(h, int(inst), _dptr(out))
+    if rc:
+        raise LbmError(rc, "lbm_freezing")
+    return out
+
+
+def lbm_solid_profile(h, inst: int, nx: int) -> np.ndarray:
+    out = np.zeros(nx)
+    rc = load().lbm_solid_profile(h, int(inst), _dptr(out))
+    if rc:
+        raise LbmError(rc, "lbm_solid_profile")
     return out
 
 
@@ -342,6 +365,20 @@ class Lattice:
 
     def observables_all(self, check: bool = True) -> np.ndarray:
         return lbm_observables_all(self._h, self.n_inst, check)
+
+    def freezing(self, inst: int = 0) -> dict:
+        """Freezing record of the run: last observable step, the FP64
+        mass-source integral over every step, the first observed step with
+        solidified fraction >= 0.99 (-1 before) and the fraction itself."""
+        v = lbm_freezing(self._h, inst)
+        out = {k: float(v[j]) for j, k in enumerate(FRZ_NAMES)}
+        out["step"] = int(out["step"])
+        out["freeze_step"] = int(out["freeze_step"])
+        return out
+
+    def solid_profile(self, inst: int = 0) -> np.ndarray:
+        """Sum over y of f_s per column at the last observable step."""
+        return lbm_solid_profile(self._h, inst, self.params[inst]["nx"])
 
     def get_state(self, inst: int = 0):
         p = self.params[inst]

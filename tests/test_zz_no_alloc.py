@@ -29,64 +29,80 @@ def env():
     return torch, lbm
 
 
-def _to_device(torch, pops, aux, L, pitch):
+def _blocked(pops, aux, L, pitch):
     """Host state (27 population planes with h_0 unshifted, 5 carried planes;
-    doubles) -> device buffers in the library's grouped FP32 layout: the
-    population buffer as 8 planes of (g_i, h_i) pairs then 8 planes of f_i,
-    the own-site buffer as (g_0, h_0 - L f_l, f_0, f_l) then
-    ((phi u)_x, (phi u)_y, p, S) per site; rows of `pitch` sites."""
+    doubles) -> the library's blocked FP32 layout: row blocks of 32 sites,
+    each holding 768 population floats (8 planes of (g_i, h_i) pairs, then 8
+    of f_i) and 320 own-site floats ((g_0, h_0 - L f_l, f_0, f_l), then
+    ((phi u)_x, (phi u)_y, p, S), then 64 unused)."""
     ny, nx = pops.shape[1:]
-    P = np.zeros((24, ny, pitch), np.float32)
-    A = np.zeros((8, ny, pitch), np.float32)
-    P4 = P[:16].reshape(8, ny, pitch, 2)  # pair planes viewed as (i, y, x, g/h)
-    for i in range(1, 9):
-        P4[i - 1, :, :nx, 0] = pops[i]
-        P4[i - 1, :, :nx, 1] = pops[9 + i]
-        P[15 + i, :, :nx] = pops[18 + i]
-    O = A.reshape(2, ny, pitch, 4)
-    O[0, :, :nx, 0] = pops[0]
-    O[0, :, :nx, 1] = pops[9] - L * aux[0]
-    O[0, :, :nx, 2] = pops[18]
-    O[0, :, :nx, 3] = aux[0]
-    for k in range(4):
-        O[1, :, :nx, k] = aux[1 + k]
-    return torch.from_numpy(P).cuda(), torch.from_numpy(A).cuda()
+    nb = pitch // 32
+
+    def wide(a):  # [k, ny, nx] -> [ny, nb, k, 32], zero beyond nx
+        w = np.zeros((a.shape[0], ny, pitch))
+        w[:, :, :nx] = a
+        return w.reshape(a.shape[0], ny, nb, 32).transpose(1, 2, 0, 3)
+
+    P = np.zeros((ny, nb, 768), np.float32)
+    A = np.zeros((ny, nb, 320), np.float32)
+    gh = P[:, :, :512].reshape(ny, nb, 8, 32, 2)
+    gh[..., 0] = wide(pops[1:9])
+    gh[..., 1] = wide(pops[10:18])
+    P[:, :, 512:] = wide(pops[19:27]).reshape(ny, nb, 256)
+    own = np.stack([pops[0], pops[9] - L * aux[0], pops[18], aux[0]])
+    A[:, :, :128] = wide(own).transpose(0, 1, 3, 2).reshape(ny, nb, 128)
+    A[:, :, 128:256] = wide(aux[1:5]).transpose(0, 1, 3, 2).reshape(ny, nb, 128)
+    return P.ravel(), A.ravel()
 
 
-def _to_host(P, A, L, nx):
-    P = P.cpu().numpy().astype(np.float64)
-    A = A.cpu().numpy().astype(np.float64)
-    _, ny, pitch = P.shape
-    P4 = P[:16].reshape(8, ny, pitch, 2)
-    O = A.reshape(2, ny, pitch, 4)
+def _unblocked(P, A, L, nx, ny, pitch):
+    nb = pitch // 32
+    P = P.astype(np.float64).reshape(ny, nb, 768)
+    A = A.astype(np.float64).reshape(ny, nb, 320)
+
+    def narrow(v):  # [ny, nb, k, 32] -> [k, ny, nx]
+        return v.transpose(2, 0, 1, 3).reshape(v.shape[2], ny, pitch)[:, :, :nx]
+
+    gh = P[:, :, :512].reshape(ny, nb, 8, 32, 2)
     pops = np.zeros((27, ny, nx))
     aux = np.zeros((5, ny, nx))
-    for i in range(1, 9):
-        pops[i] = P4[i - 1, :, :nx, 0]
-        pops[9 + i] = P4[i - 1, :, :nx, 1]
-        pops[18 + i] = P[15 + i, :, :nx]
-    aux[0] = O[0, :, :nx, 3]
-    pops[0] = O[0, :, :nx, 0]
-    pops[9] = O[0, :, :nx, 1] + L * aux[0]
-    pops[18] = O[0, :, :nx, 2]
-    for k in range(4):
-        aux[1 + k] = O[1, :, :nx, k]
+    pops[1:9] = narrow(gh[..., 0])
+    pops[10:18] = narrow(gh[..., 1])
+    pops[19:27] = narrow(P[:, :, 512:].reshape(ny, nb, 8, 32))
+    own = narrow(A[:, :, :128].reshape(ny, nb, 32, 4).transpose(0, 1, 3, 2))
+    aux[1:5] = narrow(A[:, :, 128:256].reshape(ny, nb, 32, 4).transpose(0, 1, 3, 2))
+    aux[0] = own[3]
+    pops[0], pops[9], pops[18] = own[0], own[1] + L * aux[0], own[2]
     return pops, aux
 
 
-def test_noalloc_step_matches_handle_step_twice(env):
+CASES = {
+    # sessile drop: bottom wall, periodic x, ragged blocks and tiles
+    "sessile_pitch_128": (dict(nx=100, ny=70, R=24.0, theta_deg=70.0), 128, None),
+    # the same with a pitch wider than it needs
+    "sessile_pitch_160": (dict(nx=100, ny=70, R=24.0, theta_deg=70.0), 160, None),
+    # closed box: walls on every side, no periodic axis, two Dirichlet walls
+    "closed_box": (dict(nx=45, ny=37, R=12.0, theta_deg=120.0), 64,
+                   dict(periodic_x=0, periodic_y=0, dirichlet_x_hi=1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_noalloc_step_matches_handle_step_twice(env, case):
     torch, lbm = env
-    p, phi0, T0 = inputs.sessile(nx=100, ny=70, R=24.0, theta_deg=70.0)
+    kw, pitch, over = CASES[case]
+    p, phi0, T0 = inputs.sessile(**kw)
+    if over:
+        p = dict(p, **over)
     L = p["Cp"] * (p["T_m"] - p["T_w"]) / p["Ste"]
-    pitch = (p["nx"] + 31) // 32 * 32
     lat = lbm.Lattice([p])
     lat.set_kernel(lbm.LBM_KERNEL_TILE, 32, 8)
     lat.init(phi0, T0).step(40)
     pops, aux = lat.get_state()
-
-    bufs = [_to_device(torch, pops, aux, L, pitch),
-            (torch.zeros((24, p["ny"], pitch), dtype=torch.float32, device="cuda"),
-             torch.zeros((8, p["ny"], pitch), dtype=torch.float32, device="cuda"))]
+    P0, A0 = _blocked(pops, aux, L, pitch)
+    bufs = [(torch.from_numpy(P0).cuda(), torch.from_numpy(A0).cuda()),
+            (torch.zeros(P0.size, dtype=torch.float32, device="cuda"),
+             torch.zeros(A0.size, dtype=torch.float32, device="cuda"))]
     d_obs = torch.zeros(lbm.LBM_OBS_COUNT, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
@@ -97,7 +113,8 @@ def test_noalloc_step_matches_handle_step_twice(env):
         torch.cuda.synchronize()
         lat.step(1)
         want_pops, want_aux = lat.get_state()
-        got_pops, got_aux = _to_host(Po, Ao, L, p["nx"])
+        got_pops, got_aux = _unblocked(Po.cpu().numpy(), Ao.cpu().numpy(), L, p["nx"], p["ny"],
+                                       pitch)
         assert np.abs(got_pops - want_pops).max() <= TOL, call
         assert np.abs(got_aux - want_aux).max() <= TOL, call
         got_obs = d_obs.cpu().numpy()
@@ -121,4 +138,16 @@ def test_noalloc_rejects_what_it_cannot_hold(env):
     assert e.value.code == lbm.LBM_EINVAL
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_step_noalloc(small, 0, 16, 16, 16, 64, 16, 0)  # null input
+    assert e.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step_noalloc(small, 16, 16, 16, 16, 48, 16, 0)  # pitch not a multiple of 32
+    assert e.value.code == lbm.LBM_EINVAL
+    # an output buffer that overlaps an input (pitch 64, 16 rows: 24576
+    # population floats): out starts inside in
+    base, aux = 1 << 20, 1 << 24
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step_noalloc(small, base, aux, base + 4096, aux + (1 << 22), 64, 16, 0)
+    assert e.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:  # output populations overlap the output own-site data
+        lbm.lbm_step_noalloc(small, base, aux, aux + (1 << 22) - 4096, aux + (1 << 22), 64, 16, 0)
     assert e.value.code == lbm.LBM_EINVAL
