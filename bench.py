@@ -533,9 +533,9 @@ def _batch_handle(cases, storage, dev, exec_mode, chunk, tune_steps):
     for k, (_, phi0, T0) in enumerate(cases):
         lat.init(phi0, T0, inst=k)
     lat.step(3)
-    if tune_steps:
-        lat.autotune(steps=tune_steps)
     lat.set_exec(exec_mode, chunk)
+    if tune_steps:  # timed in the form that will run (candidates' graphs are dropped)
+        lat.autotune(steps=tune_steps)
     lat.step(chunk + 1)  # captures the graph of the chosen layout
     # start the timed run from step 0, so that forms compare at equal steps
     for k, (_, phi0, T0) in enumerate(cases):

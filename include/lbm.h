@@ -250,11 +250,22 @@ int lbm_set_state(lbm_handle* h, int32_t inst, const double* pops,
    For both strip layouts b = 0 picks the rows per strip that let one wave
    of resident warps take every strip of every lattice; lbm_get_kernel
    reports the rows in effect.
+   LBM_KERNEL_BLOCK: one warp per 32-site column of the layout's row blocks
+                     (b rows each): every row it needs arrives as four bulk
+                     copies (cp.async.bulk on an mbarrier) of contiguous
+                     chunks of the rows y - 1, y, y + 1, the two columns on
+                     either side as small copies; offsets inside a staged
+                     row are compile-time constants. All storage formats;
+                     needs every lattice periodic in x. (a, c) in {(4,128),
+                     (4,168), (8,128)}.
+   For the strip and block layouts b = 0 picks the rows per item that let
+   one wave of resident warps take every item of every lattice.
    lbm_create picks STAGED (4, 0, 168) when every lattice is periodic in x,
    else TILE (32, 8). */
 #define LBM_KERNEL_TILE   0
 #define LBM_KERNEL_STRIP  1
 #define LBM_KERNEL_STAGED 2
+#define LBM_KERNEL_BLOCK  3
 
 /* Thermal type of the walls of lattice `inst` from now on (1 = held at T_w,
    0 = adiabatic; flags as in lbm_params). The paper relaxes a drop to its
@@ -347,8 +358,11 @@ int64_t lbm_launch_count(const lbm_handle* h);
    blocked state layout: sites are numbered site = y * pitch + x with pitch a
    multiple of 32 and >= nx, i.e. site = 32 blk + l (blk = site / 32 the row
    block, l = x % 32), plane = pitch * ny. pops_in/pops_out hold 24 * plane
-   floats, 768 per block: the pair (g_i, h_i) of direction i = 1..8 at
-   768 blk + 64 (i - 1) + 2 l and f_i at 768 blk + 512 + 32 (i - 1) + l;
+   floats, 768 per block in three chunks by the y component of the
+   direction: P (directions 2, 5, 6) at 0, Z (1, 3) at 288, M (4, 7, 8) at
+   480; inside a chunk of n directions the k-th (in that order) keeps its
+   pairs (g_i, h_i) at 64 k + 2 l and f_i at 64 n + 32 k + l, all offsets
+   from 768 blk;
    aux_in/aux_out hold 10 * plane floats, 320 per block: the group
    (g_0, h_0 - L f_l, f_0, f_l) at 320 blk + 4 l and ((phi u)_x, (phi u)_y,
    p, S) at 320 blk + 128 + 4 l (the last 64 floats of a block are not used;

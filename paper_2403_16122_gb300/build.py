@@ -28,7 +28,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 # sources compiled once per part, with the number of parts; a part leaves the
 # helpers that only other parts use unreferenced (diagnostic 177)
-PARTS = {"lbm_kernels.cu": 6}
+PARTS = {"lbm_kernels.cu": 9}
 PART_FLAGS = ["-diag-suppress=177"]
 
 

@@ -243,7 +243,11 @@ void build_tiles(lbm_handle* h) {
 
 // Strip items ordered by (lattice, row segment, strip) so that warps that run
 // together touch neighbouring columns of the same rows.
-bool is_strip(int kind) { return kind == LBM_KERNEL_STRIP || kind == LBM_KERNEL_STAGED; }
+bool is_strip(int kind) {
+    return kind == LBM_KERNEL_STRIP || kind == LBM_KERNEL_STAGED || kind == LBM_KERNEL_BLOCK;
+}
+// Output columns of one item of a strip-like layout.
+int item_width(int kind) { return kind == LBM_KERNEL_BLOCK ? lbmk::kBlockW : lbmk::kStripW; }
 
 // Rows per strip item: as requested, or (0) the fewest that let one wave of
 // resident warps take every item of every lattice at once.
@@ -251,12 +255,15 @@ int item_rows(const lbm_handle* h) {
     if (h->rows_req > 0) return h->rows_req;
     long long strip_rows = 0;
     int max_ny = kMinRows;
+    const int wd = item_width(h->kind);
     for (const auto& p : h->params) {
-        strip_rows += (long long)((p.nx + lbmk::kStripW - 1) / lbmk::kStripW) * p.ny;
+        strip_rows += (long long)((p.nx + wd - 1) / wd) * p.ny;
         max_ny = std::max(max_ny, p.ny);
     }
-    const int warps = lbmk::strip_resident_warps(h->kind == LBM_KERNEL_STAGED, h->warps, h->regs,
-                                                 h->storage);
+    const int warps = h->kind == LBM_KERNEL_BLOCK
+                          ? lbmk::block_resident_warps(h->warps, h->regs, h->storage)
+                          : lbmk::strip_resident_warps(h->kind == LBM_KERNEL_STAGED, h->warps,
+                                                       h->regs, h->storage);
     if (warps <= 0) return 16;
     const long long r = (strip_rows + warps - 1) / warps;
     return (int)std::min<long long>(std::max<long long>(r, kMinRows), max_ny);
@@ -269,7 +276,7 @@ void build_items(lbm_handle* h) {
         const lbm_params& p = h->params[k];
         h->inst[k].part_begin = (int)h->items.size();
         for (int y0 = 0; y0 < p.ny; y0 += h->rows)
-            for (int x0 = 0; x0 < p.nx; x0 += lbmk::kStripW) {
+            for (int x0 = 0; x0 < p.nx; x0 += item_width(h->kind)) {
                 Item it;
                 memset(&it, 0, sizeof(it));
                 it.inst = k;
@@ -342,6 +349,10 @@ int upload_tables(lbm_handle* h) {
         cudaError_t e = lbmk::prepare_staged(h->warps, h->regs, h->storage);
         if (e != cudaSuccess) return cuda_fail(e);
     }
+    if (h->kind == LBM_KERNEL_BLOCK) {
+        cudaError_t e = lbmk::prepare_block(h->warps, h->regs, h->storage);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (is_strip(h->kind)) build_items(h); else build_tiles(h);
     cudaError_t e = cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(Inst) * h->n_inst,
                                     cudaMemcpyHostToDevice, h->stream);
@@ -355,15 +366,22 @@ int upload_tables(lbm_handle* h) {
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(h->stream);  // host tables may change after return
     if (e != cudaSuccess) return cuda_fail(e);
-    h->persist_grid = is_strip(h->kind)
-                          ? lbmk::persistent_grid(h->kind == LBM_KERNEL_STAGED, h->warps, h->regs,
-                                                  h->storage, (int)h->items.size())
-                          : 0;
+    h->persist_grid = h->kind == LBM_KERNEL_BLOCK
+                          ? lbmk::block_persistent_grid(h->warps, h->regs, h->storage,
+                                                        (int)h->items.size())
+                          : (is_strip(h->kind)
+                                 ? lbmk::persistent_grid(h->kind == LBM_KERNEL_STAGED, h->warps,
+                                                         h->regs, h->storage, (int)h->items.size())
+                                 : 0);
     return LBM_OK;
 }
 
 // One time step through the ordinary kernels (obs != 0: with observable partials).
 cudaError_t enqueue_step(lbm_handle* h, int parity, int obs, cudaStream_t s) {
+    if (h->kind == LBM_KERNEL_BLOCK)
+        return lbmk::launch_step_block(h->warps, h->regs, h->storage, h->d_inst, h->d_items,
+                                       (int)h->items.size(), parity, obs, h->d_part,
+                                       &h->d_sync->err, s);
     if (h->kind == LBM_KERNEL_STAGED)
         return lbmk::launch_step_staged(h->warps, h->regs, h->storage, h->d_inst, h->d_items,
                                         (int)h->items.size(), parity, obs, h->d_part, s);
@@ -378,6 +396,11 @@ cudaError_t enqueue_step(lbm_handle* h, int parity, int obs, cudaStream_t s) {
 cudaError_t enqueue_persistent(lbm_handle* h, int parity, int n, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&h->d_sync->bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    if (h->kind == LBM_KERNEL_BLOCK)
+        return lbmk::launch_step_block_persistent(h->warps, h->regs, h->storage, h->persist_grid,
+                                                  h->d_inst, h->d_items, (int)h->items.size(),
+                                                  parity, n, &h->d_sync->bar, &h->d_sync->err,
+                                                  kBarrierLimitNs, s);
     return lbmk::launch_step_strip_persistent(h->kind == LBM_KERNEL_STAGED, h->warps, h->regs,
                                               h->storage, h->persist_grid,
                                               h->d_inst, h->d_items, (int)h->items.size(),
@@ -575,6 +598,7 @@ int lbm_step(lbm_handle* h, int64_t n) {
     if (!h->initialised) return LBM_ESTATE;
     if (h->failed) return LBM_ETIMEOUT;
     h->clock += n;
+    if (h->kind == LBM_KERNEL_BLOCK && n > 0) h->persist_pending = true;  // its error word too
     // every step but the last runs without observables, in the handle's form
     int64_t body = n > 0 ? n - 1 : 0;
     if (h->exec != LBM_EXEC_LAUNCH) {
@@ -915,11 +939,18 @@ int lbm_set_kernel(lbm_handle* h, int32_t kind, int32_t a, int32_t b, int32_t c)
         if (!lbmk::tile_supported(a, b) || h->storage != LBM_STORE_FP32) return LBM_EINVAL;
         if (h->exec == LBM_EXEC_PERSISTENT) return LBM_EINVAL;  // persistent form is strip-only
         h->kind = kind; h->tx = a; h->ty = b;
+    } else if (kind == LBM_KERNEL_BLOCK) {
+        for (int k = 0; k < h->n_inst; ++k)
+            if (!h->params[k].periodic_x) return LBM_EINVAL;
+        if (!lbmk::block_supported(a, c) || (b != 0 && b < kMinRows)) return LBM_EINVAL;
+        h->kind = kind; h->warps = a; h->rows_req = b; h->regs = c;
     } else if (kind == LBM_KERNEL_STRIP || kind == LBM_KERNEL_STAGED) {
         for (int k = 0; k < h->n_inst; ++k)
             if (!h->params[k].periodic_x) return LBM_EINVAL;
-        if (!lbmk::strip_supported(a, c) || (b != 0 && b < kMinRows)) return LBM_EINVAL;
-        if (kind == LBM_KERNEL_STAGED && !lbmk::staged_supported(a, c, h->storage)) return LBM_EINVAL;
+        if (b != 0 && b < kMinRows) return LBM_EINVAL;
+        if (kind == LBM_KERNEL_STAGED ? !lbmk::staged_supported(a, c, h->storage)
+                                      : !lbmk::strip_supported(a, c))
+            return LBM_EINVAL;
         if (kind == LBM_KERNEL_STRIP && h->storage == LBM_STORE_BF16) return LBM_EINVAL;  // staged only
         h->kind = kind; h->warps = a; h->rows_req = b; h->regs = c;
     } else {
@@ -987,6 +1018,9 @@ int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, in
             for (auto& v : var) cands.push_back({LBM_KERNEL_STRIP, v[0], r, v[1]});
         for (int r : rows)
             for (auto& v : var) cands.push_back({LBM_KERNEL_STAGED, v[0], r, v[1]});
+        const int bvar[][2] = {{4, 128}, {4, 168}, {8, 128}};
+        for (int r : rows)
+            for (auto& v : bvar) cands.push_back({LBM_KERNEL_BLOCK, v[0], r, v[1]});
     }
     if (h->exec != LBM_EXEC_PERSISTENT) {  // the persistent form is strip-only
         cands.push_back({LBM_KERNEL_TILE, 32, 8, 0});

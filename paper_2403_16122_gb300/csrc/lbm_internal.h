@@ -34,12 +34,20 @@ enum : int {
 // sites and l = x % 32 the site's place in it. Every block keeps all the
 // values of its 32 sites together (one contiguous run per block, blocks in
 // row order), so the values of a row segment share DRAM pages instead of
-// lying in 24 or more planes a whole lattice apart. Inside a block, values a
-// site pulls from the same neighbour, or keeps for itself, sit side by side,
-// so that one wide copy moves them:
+// lying in 24 or more planes a whole lattice apart.
 //   population region (kPopBlock elements of the storage type per block):
-//     (g_i, h_i) of direction i = 1..8 at 64 (i - 1) + 2 l + set,
-//     f_i at 512 + 32 (i - 1) + l                   -> 24 elements per site;
+//     three chunks by the y component of the direction a population moves
+//     along, so that a row's pull takes one contiguous chunk from each of
+//     the rows y - 1, y and y + 1:
+//       chunk P (c_y = +1: directions 2, 5, 6) at element 0,
+//       chunk Z (c_y =  0: directions 1, 3)    at element 288,
+//       chunk M (c_y = -1: directions 4, 7, 8) at element 480;
+//     inside a chunk of n directions, direction number k (in the order
+//     above) keeps its (g, h) pairs at 64 k + 2 l + set and its f at
+//     64 n + 32 k + l. Chunks P and M list opposite directions in the same
+//     order (4 = opp 2, 7 = opp 5, 8 = opp 6), so a wall's bounce-back reads
+//     the opposite chunk of the same row where the pull would read the
+//     chunk of the row behind the wall.
 //   own-site region (kAuxBlock FP32 values per block):
 //     (g_0, h_0 - L f_l, f_0, f_l) at 4 l,
 //     ((phi u)_x, (phi u)_y, p, S) at 128 + 4 l,
@@ -49,6 +57,22 @@ enum : int {
 constexpr int kPopElems = 24;
 constexpr int kPopBlock = kPopElems * 32;  // population elements per block
 constexpr int kAuxBlock = 10 * 32;         // own-site floats per block
+constexpr int kChunkP = 0, kChunkZ = 288, kChunkM = 480;  // chunk offsets (elements)
+
+// Chunk of direction i (1..8): its offset, the direction's number k inside
+// it and the chunk's number of directions n.
+__host__ __device__ constexpr int chunk_of(int i) {
+    return (i == 2 || i == 5 || i == 6) ? kChunkP : ((i == 1 || i == 3) ? kChunkZ : kChunkM);
+}
+__host__ __device__ constexpr int chunk_k(int i) {
+    return (i == 2 || i == 1 || i == 4) ? 0 : ((i == 5 || i == 3 || i == 7) ? 1 : 2);
+}
+__host__ __device__ constexpr int chunk_n(int i) { return (i == 1 || i == 3) ? 2 : 3; }
+// Offsets of (g_i, h_i) and f_i inside a block (elements).
+__host__ __device__ constexpr int gh_off(int i) { return chunk_of(i) + 64 * chunk_k(i); }
+__host__ __device__ constexpr int f_off(int i) {
+    return chunk_of(i) + 64 * chunk_n(i) + 32 * chunk_k(i);
+}
 
 // The two 16-bit storage types (FP16: 10-bit mantissa, BF16: 7-bit mantissa
 // and the FP32 exponent range) behind one set of conversions.
@@ -69,6 +93,27 @@ struct Bits16<__half> {
     static __device__ float2 unpack2(unsigned w) {
         return __half22float2(*reinterpret_cast<const __half2*>(&w));
     }
+    // mixed-precision forms (sm_100 and later): the 16-bit operand converts
+    // exactly, the result rounds once
+    static __device__ float add_lo(unsigned w, float c) {  // low half of w + c
+        float d;
+        asm("{ .reg .b16 lo, hi; mov.b32 {lo, hi}, %1; add.rn.f32.f16 %0, lo, %2; }"
+            : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
+    static __device__ float add_hi(unsigned w, float c) {  // high half of w + c
+        float d;
+        asm("{ .reg .b16 lo, hi; mov.b32 {lo, hi}, %1; add.rn.f32.f16 %0, hi, %2; }"
+            : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
+    // low half of w times 2^-12, plus c
+    static __device__ float fma_lo_2m12(unsigned w, float c) {
+        float d;
+        asm("{ .reg .b16 lo, hi, s; mov.b32 {lo, hi}, %1; mov.b16 s, 0x0C00; fma.rn.f32.f16 %0, lo, s, %2; }"
+            : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
 };
 template <>
 struct Bits16<__nv_bfloat16> {
@@ -84,12 +129,30 @@ struct Bits16<__nv_bfloat16> {
     static __device__ float2 unpack2(unsigned w) {
         return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
     }
+    static __device__ float add_lo(unsigned w, float c) {
+        float d;
+        asm("{ .reg .b16 lo, hi; mov.b32 {lo, hi}, %1; add.rn.f32.bf16 %0, lo, %2; }"
+            : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
+    static __device__ float add_hi(unsigned w, float c) {
+        float d;
+        asm("{ .reg .b16 lo, hi; mov.b32 {lo, hi}, %1; add.rn.f32.bf16 %0, hi, %2; }"
+            : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
+    static __device__ float fma_lo_2m12(unsigned w, float c) {
+        float d;
+        asm("{ .reg .b16 lo, hi, s; mov.b32 {lo, hi}, %1; mov.b16 s, 0x3980; fma.rn.f32.bf16 %0, lo, s, %2; }"
+            : "=f"(d) : "r"(w), "f"(c));
+        return d;
+    }
 };
 __host__ __device__ inline int gh_at(int i, int site, int set) {
-    return (site >> 5) * kPopBlock + 64 * (i - 1) + 2 * (site & 31) + set;
+    return (site >> 5) * kPopBlock + gh_off(i) + 2 * (site & 31) + set;
 }
 __host__ __device__ inline int f_at(int i, int site) {
-    return (site >> 5) * kPopBlock + 512 + 32 * (i - 1) + (site & 31);
+    return (site >> 5) * kPopBlock + f_off(i) + (site & 31);
 }
 __host__ __device__ inline int own0_at(int site, int c) {
     return (site >> 5) * kAuxBlock + 4 * (site & 31) + c;
@@ -169,6 +232,38 @@ struct StripPart {
                                       unsigned* d_bar, int* d_err, unsigned long long limit_ns,
                                       cudaStream_t s);
 };
+
+// The block kernels of one storage type ST (one warp per 32-site column of
+// row blocks; lattices periodic in x), for the supported (warps, regs) pairs;
+// compiled in their own part of the kernel library. d_err: raised (2) when a
+// staged row never completed, then the warp stops.
+template <typename ST>
+struct BlockPart {
+    static cudaError_t launch(int warps, int regs, const Inst* d_inst, const Item* d_items,
+                              int n_items, int parity, int obs, double* d_partials, int* d_err,
+                              cudaStream_t s);
+    static cudaError_t prepare(int warps, int regs);
+    static int resident_warps(int warps, int regs);
+    static int persist_grid(int warps, int regs, int n_items);
+    static cudaError_t persist_launch(int warps, int regs, int grid, const Inst* d_inst,
+                                      const Item* d_items, int n_items, int parity0, int nsteps,
+                                      unsigned* d_bar, int* d_err, unsigned long long limit_ns,
+                                      cudaStream_t s);
+};
+// Block items: columns [x0, x0 + 32) with x0 a multiple of 32.
+constexpr int kBlockW = 32;
+bool block_supported(int warps, int regs);
+// Raise the dynamic shared-memory limits of a block variant (host call).
+cudaError_t prepare_block(int warps, int regs, int storage);
+cudaError_t launch_step_block(int warps, int regs, int storage, const Inst* d_inst,
+                              const Item* d_items, int n_items, int parity, int obs,
+                              double* d_partials, int* d_err, cudaStream_t s);
+int block_resident_warps(int warps, int regs, int storage);
+int block_persistent_grid(int warps, int regs, int storage, int n_items);
+cudaError_t launch_step_block_persistent(int warps, int regs, int storage, int grid,
+                                         const Inst* d_inst, const Item* d_items, int n_items,
+                                         int parity0, int nsteps, unsigned* d_bar, int* d_err,
+                                         unsigned long long limit_ns, cudaStream_t s);
 
 // Launch one time step over every strip item (one warp each, `warps` warps
 // per CTA) in stream s.

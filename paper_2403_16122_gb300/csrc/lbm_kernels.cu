@@ -447,18 +447,68 @@ struct RowObs {
     __device__ __forceinline__ double total() const { return (double)s + (double)c; }
 };
 
+// Where site_update writes one site's post-collision values: by site index
+// through the layout's index functions (every kernel but the block one), or
+// at a lane of a row block whose base the caller holds (block kernel: the
+// offsets inside the block are compile-time constants).
+struct SiteStore {
+    void* B;
+    float* Baux;
+    int own;
+    __device__ __forceinline__ void gh32(int i, float g, float h) const {
+        *reinterpret_cast<float2*>(static_cast<float*>(B) + gh_at(i, own, 0)) = make_float2(g, h);
+    }
+    __device__ __forceinline__ void f32(int i, float f) const { static_cast<float*>(B)[f_at(i, own)] = f; }
+    __device__ __forceinline__ void gh16(int i, unsigned w) const {
+        *reinterpret_cast<unsigned*>(static_cast<unsigned short*>(B) + gh_at(i, own, 0)) = w;
+    }
+    __device__ __forceinline__ void f16(int i, unsigned short v) const {
+        static_cast<unsigned short*>(B)[f_at(i, own)] = v;
+    }
+    __device__ __forceinline__ void own0(float4 v) const {
+        *reinterpret_cast<float4*>(Baux + own0_at(own, 0)) = v;
+    }
+    __device__ __forceinline__ void own1(float4 v) const {
+        *reinterpret_cast<float4*>(Baux + own1_at(own, 0)) = v;
+    }
+    __device__ __forceinline__ void ref(float2 v) const {
+        *reinterpret_cast<float2*>(Baux + ref_at(own, 0)) = v;
+    }
+};
+struct BlockStore {
+    void* B;      // population block of the site's row block (elements of the storage type)
+    float* Baux;  // own-site block
+    int l;        // the site's place in the block
+    __device__ __forceinline__ void gh32(int i, float g, float h) const {
+        *reinterpret_cast<float2*>(static_cast<float*>(B) + gh_off(i) + 2 * l) = make_float2(g, h);
+    }
+    __device__ __forceinline__ void f32(int i, float f) const { static_cast<float*>(B)[f_off(i) + l] = f; }
+    __device__ __forceinline__ void gh16(int i, unsigned w) const {
+        *reinterpret_cast<unsigned*>(static_cast<unsigned short*>(B) + gh_off(i) + 2 * l) = w;
+    }
+    __device__ __forceinline__ void f16(int i, unsigned short v) const {
+        static_cast<unsigned short*>(B)[f_off(i) + l] = v;
+    }
+    __device__ __forceinline__ void own0(float4 v) const { *reinterpret_cast<float4*>(Baux + 4 * l) = v; }
+    __device__ __forceinline__ void own1(float4 v) const {
+        *reinterpret_cast<float4*>(Baux + 128 + 4 * l) = v;
+    }
+    __device__ __forceinline__ void ref(float2 v) const {
+        *reinterpret_cast<float2*>(Baux + 256 + 2 * l) = v;
+    }
+};
+
 // Eq. 38 stencils, forces (Eqs. 11-12), flow macroscopics (Eqs. 33-36), the
 // three collisions (Eqs. 21, 25, 27-28, 30-33) and the store of the
 // post-collision populations and carried fields of one site. The order of
-// every floating-point operation is fixed here, so all kernels built on it
-// produce bit-identical results.
-template <bool OBS, typename ST = float, typename Pops = ArrPops, typename Acc = ObsAcc>
-__device__ __forceinline__ void site_update(const Phys& P, int flags, const Macro& m,
-                                            const Pops& pop,
-                                            float phiux_p, float phiuy_p, const Stencil& st,
-                                            void* __restrict__ Bv, float* __restrict__ Baux,
-                                            int plane, int own, bool on_col, bool on_row,
-                                            Acc& ob, const Ref* dref = nullptr) {
+// every floating-point operation is fixed here; kernels differ only in which
+// multiply-adds the compiler contracts.
+template <bool OBS, typename ST = float, typename Pops = ArrPops, typename Acc = ObsAcc,
+          typename Store = SiteStore>
+__device__ __forceinline__ void site_update_to(const Phys& P, int flags, const Macro& m,
+                                               const Pops& pop, float phiux_p, float phiuy_p,
+                                               const Stencil& st, const Store& out, bool on_col,
+                                               bool on_row, Acc& ob, const Ref* dref = nullptr) {
     const float phi = m.phi, rho = m.rho, fs = m.fs, mdot = m.mdot;
     const float gphx = st.gphx, gphy = st.gphy, lph = st.lph, grx = st.grx, gry = st.gry;
     const float gpx = st.gpx, gpy = st.gpy, gSx = st.gSx, gSy = st.gSy;
@@ -528,7 +578,9 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
     const float TCp = T * Cp_loc, TCpref = T * P.Cpref;
     const float uu15 = 1.5f * uu;
     float g0n = 0.f, h0n = 0.f, f0n = 0.f;  // rest populations
-    float eg = 0.f, eh = 0.f, ef = 0.f;     // FP16 storage: rounding carried to them
+    // 16-bit storage: what the stored values add to the site's outgoing
+    // deviations (sum of q - d), taken back from the rest populations
+    float eg = 0.f, eh = 0.f, ef = 0.f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float w = WGT(i);
@@ -557,39 +609,36 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
         if (i == 0) {
             g0n = gn; h0n = hn; f0n = fn;  // own-site group, stored below
         } else if constexpr (sizeof(ST) == 4) {
-            float* B = static_cast<float*>(Bv);
-            *reinterpret_cast<float2*>(B + gh_at(i, own, 0)) = make_float2(gn, hn);
-            B[f_at(i, own)] = fn;
+            out.gh32(i, gn, hn);
+            out.f32(i, fn);
         } else {
             {
                 // deviations from the rest equilibria (g, h: destination's
                 // references dref[i]; f: this site's pressure), and what their
                 // rounding to 16 bits takes away from what the site sends
                 using C16 = Bits16<ST>;
-                unsigned short* B = static_cast<unsigned short*>(Bv);
                 const Ref& d = dref[i];
                 const float dg = gn - w * d.phi, dh = hn - w * P.Cpref * d.T;
                 const float df = (fn - f_rest(i, pn)) * kFScale;
                 const unsigned qgh = C16::pack2(dg, dh);  // (g_i, h_i) in one word
                 const ST qf = C16::from_f(df);
-                *reinterpret_cast<unsigned*>(B + gh_at(i, own, 0)) = qgh;
-                B[f_at(i, own)] = C16::bits(qf);
-                const float2 rgh = C16::unpack2(qgh);
-                eg += dg - rgh.x;
-                eh += dh - rgh.y;
-                ef += df - C16::to_f(qf);
+                out.gh16(i, qgh);
+                out.f16(i, C16::bits(qf));
+                eg = C16::add_lo(qgh, eg - dg);
+                eh = C16::add_hi(qgh, eh - dh);
+                ef = C16::add_lo((unsigned)C16::bits(qf), ef - df);
             }
         }
     }
     if constexpr (sizeof(ST) != 4) {  // the rest populations carry the rounding
-        g0n += eg;
-        h0n += eh;
-        f0n += ef * kInvFScale;
+        g0n -= eg;
+        h0n -= eh;
+        f0n -= ef * kInvFScale;
     }
-    *reinterpret_cast<float4*>(Baux + own0_at(own, 0)) = make_float4(g0n, h0n, f0n, m.fl);
-    *reinterpret_cast<float4*>(Baux + own1_at(own, 0)) = make_float4(phiux, phiuy, pn, S);
+    out.own0(make_float4(g0n, h0n, f0n, m.fl));
+    out.own1(make_float4(phiux, phiuy, pn, S));
     if constexpr (sizeof(ST) != 4)  // references of this site for the next step
-        *reinterpret_cast<float2*>(Baux + ref_at(own, 0)) = make_float2(phi, T);
+        out.ref(make_float2(phi, T));
 
     if (OBS) {
         ob.add(0, phi);
@@ -610,6 +659,17 @@ __device__ __forceinline__ void site_update(const Phys& P, int flags, const Macr
                          !isfinite(pn);
         if (bad) ob.add(10, 1.f);
     }
+}
+
+template <bool OBS, typename ST = float, typename Pops = ArrPops, typename Acc = ObsAcc>
+__device__ __forceinline__ void site_update(const Phys& P, int flags, const Macro& m,
+                                            const Pops& pop,
+                                            float phiux_p, float phiuy_p, const Stencil& st,
+                                            void* __restrict__ Bv, float* __restrict__ Baux,
+                                            int /*plane*/, int own, bool on_col, bool on_row,
+                                            Acc& ob, const Ref* dref = nullptr) {
+    site_update_to<OBS, ST>(P, flags, m, pop, phiux_p, phiuy_p, st, SiteStore{Bv, Baux, own}, on_col,
+                            on_row, ob, dref);
 }
 
 // ---------------------------------------------------------------------------
@@ -677,14 +737,13 @@ __device__ __forceinline__ void tile_step(const Inst& I, const Tile& T, int pari
         k -= th;
         if (k < th) { ox = tw; oy = k; return; }
         k -= th;
-        // wall extras, 4 per touched wall
+        // wall extras, 4 per touched wall, in the order y lo, y hi, x lo, x hi
         int w = k >> 2, j = k & 3;
-        int wl[4], nw = 0;
-        if (wylo) wl[nw++] = 0;
-        if (wyhi) wl[nw++] = 1;
-        if (wxlo) wl[nw++] = 2;
-        if (wxhi) wl[nw++] = 3;
-        int side = wl[w];
+        int side = 0;
+        for (int t = 0, seen = 0; t < 4; ++t) {  // the w-th touched wall
+            const bool touched = t == 0 ? wylo : (t == 1 ? wyhi : (t == 2 ? wxlo : wxhi));
+            if (touched && seen++ == w) side = t;
+        }
         int a = (j & 1), b = (j >> 1);   // a: layer (adjacent/next), b: which end
         if (side == 0) { ox = b ? tw + 1 : -2; oy = a; }
         else if (side == 1) { ox = b ? tw + 1 : -2; oy = th - 1 - a; }
@@ -1008,41 +1067,61 @@ __device__ __forceinline__ void cp_async_wait() {
 // shares with the item below it are read by this item first and by that one
 // at the end of the step; they are kept in L2 (1) until then and released (2)
 // by the second read.
+// Offsets of the blocked layout split into a column part, fixed for a lane
+// over a strip item, and a row part (pitch is a multiple of 32, so a site's
+// block is row * (pitch / 32) + column / 32): element offset = row term +
+// column term + the plane's offset inside the block.
+struct ColTerms {
+    int gh[3], f[3], aux, ref;  // columns x - 1, x, x + 1 (gh, f); the lane's own (aux, ref)
+    __device__ __forceinline__ ColTerms(int xm, int xc, int xp) {
+        const int c[3] = {xm, xc, xp};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gh[k] = (c[k] >> 5) * kPopBlock + 2 * (c[k] & 31);
+            f[k] = (c[k] >> 5) * kPopBlock + (c[k] & 31);
+        }
+        aux = (xc >> 5) * kAuxBlock + 4 * (xc & 31);
+        ref = (xc >> 5) * kAuxBlock + 256 + 2 * (xc & 31);
+    }
+};
+
 template <typename ST, bool NC>
-__device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, int xc, int xm, int xp,
-                                          bool py, int r, bool macro_only, float* slot,
-                                          int hint = 0) {
+__device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, const ColTerms& ct, bool py,
+                                          int r, bool macro_only, float* slot, int hint = 0) {
     constexpr bool kHalf = sizeof(ST) != 4;
-    const int ny = l.ny, plane = l.plane;
+    const int ny = l.ny, nxb = l.pitch >> 5;
     const bool wlo = !py && r == 0, whi = !py && r == ny - 1;
     const int rr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
     const int ym = rr == 0 ? ny - 1 : rr - 1, yp = rr == ny - 1 ? 0 : rr + 1;
-    const int o0 = rr * l.pitch, om = ym * l.pitch, op = yp * l.pitch;
-    const int own = o0 + xc;
+    // row terms of the rows y, y - 1, y + 1
+    const int t0 = rr * nxb * kPopBlock, tm = ym * nxb * kPopBlock, tp = yp * nxb * kPopBlock;
+    const int ra = rr * nxb * kAuxBlock;
     const unsigned long long pol = l2_policy(hint);
-    cp_async_p<16>(slot + 4 * lane, l.Aaux + own0_at(own, 0), pol);
-    cp_async_p<16>(slot + kSlotO1 + 4 * lane, l.Aaux + own1_at(own, 0), pol);
-    if constexpr (kHalf) cp_async_p<8>(slot + kSlotR + 2 * lane, l.Aaux + ref_at(own, 0), pol);
+    cp_async_p<16>(slot + 4 * lane, l.Aaux + ra + ct.aux, pol);
+    cp_async_p<16>(slot + kSlotO1 + 4 * lane, l.Aaux + ra + ct.aux + 128, pol);
+    if constexpr (kHalf) cp_async_p<8>(slot + kSlotR + 2 * lane, l.Aaux + ra + ct.ref, pol);
     const unsigned short* A16 = reinterpret_cast<const unsigned short*>(l.A);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int cy = CY(i), cx = CX(i);
         const bool wall = (cy > 0 && wlo) || (cy < 0 && whi);
         const int si = wall ? OPP(i) : i;
-        const int site = wall ? own : (cy > 0 ? om : (cy < 0 ? op : o0)) +
-                                          (cx > 0 ? xm : (cx < 0 ? xp : xc));
+        // source: the site itself (bounce-back) or x - c_i in row y - c_iy
+        // (the column index is a constant: no array indexed at run time)
+        const int k = cx > 0 ? 0 : (cx < 0 ? 2 : 1);
+        const int rt = wall ? t0 : (cy > 0 ? tm : (cy < 0 ? tp : t0));
+        const int cg = wall ? ct.gh[1] : ct.gh[k], cf = wall ? ct.f[1] : ct.f[k];
+        const int eg = rt + cg + gh_off(si), ef = rt + cf + f_off(si);
         if constexpr (kHalf) {
-            // planes and rows hold an even number of 16-bit values, so every
-            // aligned word lies inside its row
-            cp_async_p<4>(slot + slot_gh(i, lane),
-                          reinterpret_cast<const float*>(A16 + gh_at(si, site, 0)), pol);
+            // blocks and plane rows hold an even number of 16-bit values, so
+            // every aligned word lies inside its plane row
+            cp_async_p<4>(slot + slot_gh(i, lane), reinterpret_cast<const float*>(A16 + eg), pol);
             if (!macro_only)
-                cp_async_p<4>(slot + slot_f(i, lane),
-                              reinterpret_cast<const float*>(A16 + (f_at(si, site) & ~1)),
+                cp_async_p<4>(slot + slot_f(i, lane), reinterpret_cast<const float*>(A16 + (ef & ~1)),
                               pol);
         } else {
-            cp_async_p<8>(slot + slot_gh(i, lane), l.A + gh_at(si, site, 0), pol);
-            if (!macro_only) cp_async_p<4>(slot + slot_f(i, lane), l.A + f_at(si, site), pol);
+            cp_async_p<8>(slot + slot_gh(i, lane), l.A + eg, pol);
+            if (!macro_only) cp_async_p<4>(slot + slot_f(i, lane), l.A + ef, pol);
         }
     }
 }
@@ -1088,9 +1167,7 @@ __device__ __forceinline__ void staged_set(const float* slot, int lane, int r, i
         } else {
             const unsigned w = __float_as_uint(slot[slot_f(i, lane)]);
             const unsigned sel = wall ? par.c : (CX(i) > 0 ? par.m : (CX(i) < 0 ? par.p : par.c));
-            const float raw =
-                Bits16<ST>::to_f(Bits16<ST>::from_bits((unsigned short)__byte_perm(w, 0u, sel)));
-            v[i] = raw * kInvFScale + f_rest(i, wall ? pref[0] : pref[i]);
+            v[i] = Bits16<ST>::fma_lo_2m12(__byte_perm(w, 0u, sel), f_rest(i, wall ? pref[0] : pref[i]));
         }
         if (SET == 1 && wall) {
             const bool dir = (wlo && (flags & kDirYlo)) || (whi && (flags & kDirYhi));
@@ -1113,9 +1190,9 @@ __device__ __forceinline__ void staged_gh(const float* slot, int lane, int r, in
     h[0] = slot[4 * lane + 1];
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const float2 raw = Bits16<ST>::unpack2(__float_as_uint(slot[slot_gh(i, lane)]));
-        g[i] = raw.x + WGT(i) * ref.phi;
-        h[i] = raw.y + WGT(i) * Cpref * ref.T;
+        const unsigned wd = __float_as_uint(slot[slot_gh(i, lane)]);
+        g[i] = Bits16<ST>::add_lo(wd, WGT(i) * ref.phi);
+        h[i] = Bits16<ST>::add_hi(wd, WGT(i) * Cpref * ref.T);
         const bool wall = (CY(i) > 0 && wlo) || (CY(i) < 0 && whi);
         if (wall && dir) h[i] = -h[i] + 2.0f * WGT(i) * abb;
     }
@@ -1154,6 +1231,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     c.py = (l.flags & kPeriodicY) != 0;
     const bool out_lane = lane >= 1 && lane <= kStripW && xl < nx;
     const bool halo_lane = lane == 0 || lane == 31;
+    const ColTerms ct(c.xm, c.xc, c.xp);
     const int x_outer = lane == 0 ? c.xm : c.xp;   // one column beyond the strip
 
     // decoding references of a site (FP16 storage)
@@ -1202,7 +1280,7 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     auto issue = [&](int j) {
         if constexpr (STG > 0) {
             if (j < R && (j > 0 || has_lo) && (j < R - 1 || has_hi))
-                stage_row<ST>(l, lane, c.xc, c.xm, c.xp, c.py, y0 - 1 + j, j == 0 || j == R - 1,
+                stage_row<ST>(l, lane, ct, c.py, y0 - 1 + j, j == 0 || j == R - 1,
                               slot(j), j <= 1 ? 1 : (j >= R - 2 ? 2 : 0));
             cp_async_commit();  // possibly empty: one group per ring index
         }
@@ -1520,6 +1598,70 @@ step_strip_persistent(const Inst* __restrict__ insts, const Item* __restrict__ i
         if (s + 1 < nsteps &&
             !grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, err, limit_ns))
             return;
+    }
+}
+
+#include "lbm_block.cuh"
+
+// Block step: one warp per block item (a 32-site column of row blocks over a
+// segment of rows), every offset inside a staged row a compile-time constant.
+// Launched with programmatic dependent launch like the staged strips.
+template <int WARPS, int MINB, bool OBS, typename ST>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+step_block(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items, int parity,
+           double* __restrict__ partials, int* err) {
+    extern __shared__ __align__(16) unsigned char block_smem[];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    using BW = BlockWarp<ST>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = block_smem + warp * BW::kBytes;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + BW::kMbar);
+    if (lane == 0)
+        for (int k = 0; k < kBlockStg; ++k) mbar_init(mbar + k, 33);  // expect_tx + 32 lanes
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+    const int it = blockIdx.x * WARPS + warp;
+    if (it >= n_items) return;  // whole warp leaves together; no block barrier in the body
+    unsigned phase = 0;
+    block_item<OBS, ST, true>(insts, items[it], parity, partials, base, mbar, phase,
+                              reinterpret_cast<float*>(base + BW::kHring),
+                              reinterpret_cast<float*>(base + BW::kMd), err);
+}
+
+// Persistent form of the block step: every item of every lattice for nsteps
+// steps in one cooperative launch, a device-wide barrier between steps. The
+// staged rows are read by bulk copies (through L2, after a proxy fence that
+// orders them behind the barrier's acquire); the few global loads of the
+// side columns next to a wall bypass L1.
+template <int WARPS, int MINB, typename ST>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+step_block_persistent(const Inst* __restrict__ insts, const Item* __restrict__ items, int n_items,
+                      int parity0, int nsteps, unsigned* bar, int* err,
+                      unsigned long long limit_ns) {
+    extern __shared__ __align__(16) unsigned char block_smem[];
+    using BW = BlockWarp<ST>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = block_smem + warp * BW::kBytes;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + BW::kMbar);
+    if (lane == 0)
+        for (int k = 0; k < kBlockStg; ++k) mbar_init(mbar + k, 33);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+    unsigned phase = 0;
+    const int gw = blockIdx.x * WARPS + warp;
+    const int stride = gridDim.x * WARPS;
+    bool ok = true;
+    for (int s = 0; s < nsteps; ++s) {
+        const int parity = parity0 ^ (s & 1);
+        for (int it = gw; ok && it < n_items; it += stride)
+            ok = block_item<false, ST, false>(insts, items[it], parity, nullptr, base, mbar, phase,
+                                              reinterpret_cast<float*>(base + BW::kHring),
+                                              reinterpret_cast<float*>(base + BW::kMd), err);
+        if (s + 1 < nsteps) {
+            if (!grid_barrier(bar, (unsigned)(s + 1) * gridDim.x, err, limit_ns)) return;
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
     }
 }
 
@@ -1864,6 +2006,84 @@ auto persist_dispatch_bf16(int regs, F&& f) -> decltype(f(Persist<4, 3, 4, bf16>
     return f(Persist<4, 3, 4, bf16>());
 }
 
+// Block launches: the (warps, regs) variants.
+template <int WARPS, int MINB, typename ST>
+struct Block {
+    static constexpr int kSmem = WARPS * BlockWarp<ST>::kBytes;
+    static cudaError_t prepare() {
+        cudaError_t e = cudaFuncSetAttribute(step_block<WARPS, MINB, false, ST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_block<WARPS, MINB, true, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_block_persistent<WARPS, MINB, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        return e;
+    }
+    static int resident_warps() {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (prepare() != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, step_block<WARPS, MINB, false, ST>, WARPS * 32, kSmem) != cudaSuccess)
+            return 0;
+        return per_sm * sms * WARPS;
+    }
+    static cudaError_t launch(const Inst* d_inst, const Item* d_items, int n_items, int parity,
+                              int obs, double* d_partials, int* d_err, cudaStream_t s) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((n_items + WARPS - 1) / WARPS);
+        cfg.blockDim = dim3(WARPS * 32);
+        cfg.dynamicSmemBytes = kSmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (obs)
+            return cudaLaunchKernelEx(&cfg, step_block<WARPS, MINB, true, ST>, d_inst, d_items, n_items,
+                                      parity, d_partials, d_err);
+        return cudaLaunchKernelEx(&cfg, step_block<WARPS, MINB, false, ST>, d_inst, d_items, n_items,
+                                  parity, d_partials, d_err);
+    }
+    static int grid(int n_items) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (prepare() != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, step_block_persistent<WARPS, MINB, ST>, WARPS * 32, kSmem) != cudaSuccess)
+            return 0;
+        const int want = (n_items + WARPS - 1) / WARPS;
+        return std::max(1, std::min(want, per_sm * sms));
+    }
+    static cudaError_t persist(int grid, const Inst* d_inst, const Item* d_items, int n_items,
+                               int parity0, int nsteps, unsigned* bar, int* err,
+                               unsigned long long limit_ns, cudaStream_t s) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(WARPS * 32);
+        cfg.dynamicSmemBytes = kSmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, step_block_persistent<WARPS, MINB, ST>, d_inst, d_items,
+                                  n_items, parity0, nsteps, bar, err, limit_ns);
+    }
+};
+template <typename ST, typename F>
+auto block_dispatch(int warps, int regs, F&& f) -> decltype(f(Block<4, 4, ST>())) {
+    if (warps == 4 && regs == 168) return f(Block<4, 3, ST>());
+    if (warps == 8 && regs == 128) return f(Block<8, 2, ST>());
+    return f(Block<4, 4, ST>());
+}
+
 // The staged or plain strip variants of one storage type, each reached by
 // (warps, regs); the calls check nothing (the dispatchers below do).
 template <typename ST, bool STAGED>
@@ -1967,6 +2187,56 @@ template struct StripPart<__nv_bfloat16, true>;
 #endif
 
 // ---------------------------------------------------------------------------
+// The block kernels of one storage type, as compiled in their part
+// ---------------------------------------------------------------------------
+#if LBM_PART < 0 || LBM_PART >= 6
+template <typename ST>
+cudaError_t BlockPart<ST>::launch(int warps, int regs, const Inst* d_inst, const Item* d_items,
+                                  int n_items, int parity, int obs, double* d_partials, int* d_err,
+                                  cudaStream_t s) {
+    auto go = [&](auto v) {
+        return decltype(v)::launch(d_inst, d_items, n_items, parity, obs, d_partials, d_err, s);
+    };
+    return block_dispatch<ST>(warps, regs, go);
+}
+template <typename ST>
+cudaError_t BlockPart<ST>::prepare(int warps, int regs) {
+    auto go = [](auto v) { return decltype(v)::prepare(); };
+    return block_dispatch<ST>(warps, regs, go);
+}
+template <typename ST>
+int BlockPart<ST>::resident_warps(int warps, int regs) {
+    auto go = [](auto v) { return decltype(v)::resident_warps(); };
+    return block_dispatch<ST>(warps, regs, go);
+}
+template <typename ST>
+int BlockPart<ST>::persist_grid(int warps, int regs, int n_items) {
+    auto go = [&](auto v) { return decltype(v)::grid(n_items); };
+    return block_dispatch<ST>(warps, regs, go);
+}
+template <typename ST>
+cudaError_t BlockPart<ST>::persist_launch(int warps, int regs, int grid, const Inst* d_inst,
+                                          const Item* d_items, int n_items, int parity0, int nsteps,
+                                          unsigned* d_bar, int* d_err, unsigned long long limit_ns,
+                                          cudaStream_t s) {
+    auto go = [&](auto v) {
+        return decltype(v)::persist(grid, d_inst, d_items, n_items, parity0, nsteps, d_bar, d_err,
+                                    limit_ns, s);
+    };
+    return block_dispatch<ST>(warps, regs, go);
+}
+#endif
+#if LBM_PART == 6 || LBM_PART < 0
+template struct BlockPart<float>;
+#endif
+#if LBM_PART == 7 || LBM_PART < 0
+template struct BlockPart<__half>;
+#endif
+#if LBM_PART == 8 || LBM_PART < 0
+template struct BlockPart<__nv_bfloat16>;
+#endif
+
+// ---------------------------------------------------------------------------
 // Storage dispatch and the tile, initialisation and reduction kernels
 // ---------------------------------------------------------------------------
 #if LBM_HAS_PART(0)
@@ -2056,6 +2326,63 @@ cudaError_t launch_step_strip_persistent(int staged, int warps, int regs, int st
     if (storage == LBM_STORE_BF16) return cudaErrorInvalidValue;
     if (storage != LBM_STORE_FP32 && storage != LBM_STORE_FP16) return cudaErrorNotSupported;
     return on_storage<false>(storage, go);
+}
+
+
+namespace {
+template <typename F>
+auto on_block_storage(int storage, F&& f) {
+    if (storage == LBM_STORE_FP16) return f(BlockPart<__half>());
+    if (storage == LBM_STORE_BF16) return f(BlockPart<__nv_bfloat16>());
+    return f(BlockPart<float>());
+}
+}  // namespace
+
+bool block_supported(int warps, int regs) {
+    return (warps == 4 && (regs == 128 || regs == 168)) || (warps == 8 && regs == 128);
+}
+
+cudaError_t prepare_block(int warps, int regs, int storage) {
+    if (!block_supported(warps, regs)) return cudaErrorInvalidValue;
+    auto go = [&](auto part) { return decltype(part)::prepare(warps, regs); };
+    return on_block_storage(storage, go);
+}
+
+cudaError_t launch_step_block(int warps, int regs, int storage, const Inst* d_inst,
+                              const Item* d_items, int n_items, int parity, int obs,
+                              double* d_partials, int* d_err, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (!block_supported(warps, regs)) return cudaErrorInvalidValue;
+    auto go = [&](auto part) {
+        return decltype(part)::launch(warps, regs, d_inst, d_items, n_items, parity, obs, d_partials,
+                                      d_err, s);
+    };
+    return on_block_storage(storage, go);
+}
+
+int block_resident_warps(int warps, int regs, int storage) {
+    if (!block_supported(warps, regs)) return 0;
+    auto go = [&](auto part) { return decltype(part)::resident_warps(warps, regs); };
+    return on_block_storage(storage, go);
+}
+
+int block_persistent_grid(int warps, int regs, int storage, int n_items) {
+    if (!block_supported(warps, regs) || n_items <= 0) return 0;
+    auto go = [&](auto part) { return decltype(part)::persist_grid(warps, regs, n_items); };
+    return on_block_storage(storage, go);
+}
+
+cudaError_t launch_step_block_persistent(int warps, int regs, int storage, int grid,
+                                         const Inst* d_inst, const Item* d_items, int n_items,
+                                         int parity0, int nsteps, unsigned* d_bar, int* d_err,
+                                         unsigned long long limit_ns, cudaStream_t s) {
+    if (!block_supported(warps, regs) || grid <= 0) return cudaErrorInvalidValue;
+    if (n_items <= 0 || nsteps <= 0) return cudaSuccess;
+    auto go = [&](auto part) {
+        return decltype(part)::persist_launch(warps, regs, grid, d_inst, d_items, n_items, parity0,
+                                              nsteps, d_bar, d_err, limit_ns, s);
+    };
+    return on_block_storage(storage, go);
 }
 
 cudaError_t launch_barrier_timeout_probe(unsigned* d_bar, int* d_err, unsigned long long limit_ns,

@@ -74,7 +74,7 @@ SYMBOLS = (
     "lbm_set_exec", "lbm_get_exec", "lbm_barrier_selftest", "lbm_set_thermal_walls",
     "lbm_freezing", "lbm_solid_profile",
 )
-LBM_KERNEL_TILE, LBM_KERNEL_STRIP, LBM_KERNEL_STAGED = 0, 1, 2
+LBM_KERNEL_TILE, LBM_KERNEL_STRIP, LBM_KERNEL_STAGED, LBM_KERNEL_BLOCK = 0, 1, 2, 3
 LBM_EXEC_LAUNCH, LBM_EXEC_GRAPH, LBM_EXEC_PERSISTENT = 0, 1, 2
 
 

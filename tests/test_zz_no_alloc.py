@@ -29,29 +29,40 @@ def env():
     return torch, lbm
 
 
+# Offsets inside a block of 768 population floats: chunks by the y component
+# of the direction (P: 2, 5, 6 at 0; Z: 1, 3 at 288; M: 4, 7, 8 at 480); in a
+# chunk of n directions the k-th keeps (g, h) pairs at 64 k + 2 l and f at
+# 64 n + 32 k + l.
+CHUNK = {2: (0, 0, 3), 5: (0, 1, 3), 6: (0, 2, 3), 1: (288, 0, 2), 3: (288, 1, 2),
+         4: (480, 0, 3), 7: (480, 1, 3), 8: (480, 2, 3)}
+GH_OFF = {i: c + 64 * k for i, (c, k, n) in CHUNK.items()}
+F_OFF = {i: c + 64 * n + 32 * k for i, (c, k, n) in CHUNK.items()}
+
+
 def _blocked(pops, aux, L, pitch):
     """Host state (27 population planes with h_0 unshifted, 5 carried planes;
     doubles) -> the library's blocked FP32 layout: row blocks of 32 sites,
-    each holding 768 population floats (8 planes of (g_i, h_i) pairs, then 8
-    of f_i) and 320 own-site floats ((g_0, h_0 - L f_l, f_0, f_l), then
-    ((phi u)_x, (phi u)_y, p, S), then 64 unused)."""
+    each holding 768 population floats (the chunks above) and 320 own-site
+    floats ((g_0, h_0 - L f_l, f_0, f_l), then ((phi u)_x, (phi u)_y, p, S),
+    then 64 unused)."""
     ny, nx = pops.shape[1:]
     nb = pitch // 32
 
-    def wide(a):  # [k, ny, nx] -> [ny, nb, k, 32], zero beyond nx
-        w = np.zeros((a.shape[0], ny, pitch))
-        w[:, :, :nx] = a
-        return w.reshape(a.shape[0], ny, nb, 32).transpose(1, 2, 0, 3)
+    def wide(a):  # [ny, nx] -> [ny, nb, 32], zero beyond nx
+        w = np.zeros((ny, pitch))
+        w[:, :nx] = a
+        return w.reshape(ny, nb, 32)
 
     P = np.zeros((ny, nb, 768), np.float32)
     A = np.zeros((ny, nb, 320), np.float32)
-    gh = P[:, :, :512].reshape(ny, nb, 8, 32, 2)
-    gh[..., 0] = wide(pops[1:9])
-    gh[..., 1] = wide(pops[10:18])
-    P[:, :, 512:] = wide(pops[19:27]).reshape(ny, nb, 256)
-    own = np.stack([pops[0], pops[9] - L * aux[0], pops[18], aux[0]])
-    A[:, :, :128] = wide(own).transpose(0, 1, 3, 2).reshape(ny, nb, 128)
-    A[:, :, 128:256] = wide(aux[1:5]).transpose(0, 1, 3, 2).reshape(ny, nb, 128)
+    for i in range(1, 9):
+        P[:, :, GH_OFF[i]:GH_OFF[i] + 64:2] = wide(pops[i])
+        P[:, :, GH_OFF[i] + 1:GH_OFF[i] + 64:2] = wide(pops[9 + i])
+        P[:, :, F_OFF[i]:F_OFF[i] + 32] = wide(pops[18 + i])
+    own = [pops[0], pops[9] - L * aux[0], pops[18], aux[0]]
+    for c in range(4):
+        A[:, :, c:128:4] = wide(own[c])
+        A[:, :, 128 + c:256:4] = wide(aux[1 + c])
     return P.ravel(), A.ravel()
 
 
@@ -60,17 +71,18 @@ def _unblocked(P, A, L, nx, ny, pitch):
     P = P.astype(np.float64).reshape(ny, nb, 768)
     A = A.astype(np.float64).reshape(ny, nb, 320)
 
-    def narrow(v):  # [ny, nb, k, 32] -> [k, ny, nx]
-        return v.transpose(2, 0, 1, 3).reshape(v.shape[2], ny, pitch)[:, :, :nx]
+    def narrow(v):  # [ny, nb, 32] -> [ny, nx]
+        return v.reshape(ny, pitch)[:, :nx]
 
-    gh = P[:, :, :512].reshape(ny, nb, 8, 32, 2)
     pops = np.zeros((27, ny, nx))
     aux = np.zeros((5, ny, nx))
-    pops[1:9] = narrow(gh[..., 0])
-    pops[10:18] = narrow(gh[..., 1])
-    pops[19:27] = narrow(P[:, :, 512:].reshape(ny, nb, 8, 32))
-    own = narrow(A[:, :, :128].reshape(ny, nb, 32, 4).transpose(0, 1, 3, 2))
-    aux[1:5] = narrow(A[:, :, 128:256].reshape(ny, nb, 32, 4).transpose(0, 1, 3, 2))
+    for i in range(1, 9):
+        pops[i] = narrow(P[:, :, GH_OFF[i]:GH_OFF[i] + 64:2])
+        pops[9 + i] = narrow(P[:, :, GH_OFF[i] + 1:GH_OFF[i] + 64:2])
+        pops[18 + i] = narrow(P[:, :, F_OFF[i]:F_OFF[i] + 32])
+    own = [narrow(A[:, :, c:128:4]) for c in range(4)]
+    for c in range(4):
+        aux[1 + c] = narrow(A[:, :, 128 + c:256:4])
     aux[0] = own[3]
     pops[0], pops[9], pops[18] = own[0], own[1] + L * aux[0], own[2]
     return pops, aux
