@@ -352,6 +352,12 @@ def run_ours(args, dist: Dist):
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_lu * sites / (ms / args.steps * 1e-3) / 1e9
     traffic, traffic_kernel = profiled_traffic(workload)
+    # counters taken on another kernel family say nothing about this one
+    family = {lbm.LBM_KERNEL_TILE: "step_fp32<", lbm.LBM_KERNEL_STRIP: "step_strip<",
+              lbm.LBM_KERNEL_STAGED: "step_strip_staged<",
+              lbm.LBM_KERNEL_BLOCK: "step_block<"}.get(int(kernel[0]))
+    if traffic_kernel is None or family is None or not traffic_kernel.startswith(family):
+        traffic, traffic_kernel = None, None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 # the variant the counters were taken on (the autotuner may pick
@@ -496,7 +502,7 @@ def run_ours(args, dist: Dist):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
-            "kernel": {"kind": {0: "tile", 1: "strip", 2: "staged"}.get(kernel[0], str(kernel[0])),
+            "kernel": {"kind": {0: "tile", 1: "strip", 2: "staged", 3: "block"}.get(kernel[0], str(kernel[0])),
                        "params": list(kernel[1:]),
                        "autotune_ms_per_step": tune},
             "clocks": clocks.summary(),
