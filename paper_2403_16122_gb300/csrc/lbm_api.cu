@@ -87,8 +87,8 @@ size_t dest_site(const lbm_params& p, int x, int y, int i) {
 
 struct Layout {
     uint64_t inst_off, tile_off, item_off, part_off, obs_off, stage_off, sync_off;
-    uint64_t macc_off, frz_off, prof_off, prof_bytes;
-    std::vector<uint64_t> prof_at;  // doubles from prof_off to each lattice's profile
+    uint64_t macc_off, frz_off, prof_off, prof_out_off, prof_bytes, red_off, cnt_off, cnt_end;
+    std::vector<uint64_t> prof_at;  // doubles from prof_off (prof_out_off) to each lattice's profile
     std::vector<uint64_t> pop_off[2], aux_off[2];
     uint64_t total;
     int max_tiles, max_items, max_parts, max_sites;
@@ -131,6 +131,12 @@ Layout make_layout(const lbm_params* p, int n, int storage) {
     for (int k = 0; k < n; ++k) { L.prof_at[k] = prof_n; prof_n += (uint64_t)p[k].nx; }
     L.prof_bytes = sizeof(double) * prof_n;
     L.prof_off = off; off = align_up(off + L.prof_bytes);
+    L.prof_out_off = off; off = align_up(off + L.prof_bytes);
+    // the observable reduction's per-CTA sums and per-lattice arrival counts
+    L.red_off = off;
+    off = align_up(off + sizeof(double) * (lbmk::kObs + 1) *
+                             (uint64_t)lbmk::reduce_slots(L.max_parts, n));
+    L.cnt_off = off; L.cnt_end = off + sizeof(unsigned) * (uint64_t)n; off = align_up(L.cnt_end);
     for (int b = 0; b < 2; ++b) {
         L.pop_off[b].resize(n);
         L.aux_off[b].resize(n);
@@ -171,7 +177,11 @@ struct lbm_handle {
     double* d_stage = nullptr;
     double* d_macc = nullptr;  // running mdot sum per partial slot
     double* d_frz = nullptr;   // freezing records (kFrz doubles per lattice)
-    double* d_prof = nullptr;  // column profiles of f_s (nx doubles per lattice)
+    double* d_prof = nullptr;  // column profiles of f_s being summed (nx doubles per lattice)
+    double* d_prof_out = nullptr;  // the profiles of the last observable step
+    double* d_red = nullptr;   // per-CTA sums of the observable reduction
+    unsigned* d_cnt = nullptr; // its per-lattice arrival counts
+    int max_lattice_parts = 0; // most observable partials of one lattice
     double* h_frz = nullptr;   // pinned mirror of d_frz
     std::vector<double> mdot_base;  // mdot summed out of retired slot tables, per lattice
     std::vector<double> frz_base;   // mdot_base as of the last observable step
@@ -213,6 +223,7 @@ void fill_inst(lbm_handle* h, int k) {
     I.part_stride = h->layout.max_parts;
     I.macc = h->d_macc;
     I.prof = h->d_prof + h->layout.prof_at[k];
+    I.prof_out = h->d_prof_out + h->layout.prof_at[k];
     for (int b = 0; b < 2; ++b) {
         I.pop[b] = h->ws + h->layout.pop_off[b][k];
         I.aux[b] = reinterpret_cast<float*>(h->ws + h->layout.aux_off[b][k]);
@@ -327,6 +338,9 @@ int restart_records(lbm_handle* h, int k) {
     if (I.part_end > I.part_begin)
         e = cudaMemsetAsync(h->d_macc + I.part_begin, 0,
                             sizeof(double) * (size_t)(I.part_end - I.part_begin), h->stream);
+    if (e == cudaSuccess)  // an accumulator left by a failed call starts clean
+        e = cudaMemsetAsync(h->d_prof + h->layout.prof_at[k], 0,
+                            sizeof(double) * (size_t)h->params[k].nx, h->stream);
     const double rec[lbmk::kFrz] = {0.0, 0.0, -1.0, 0.0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_frz + (size_t)k * lbmk::kFrz, rec, sizeof(rec),
@@ -354,6 +368,10 @@ int upload_tables(lbm_handle* h) {
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (is_strip(h->kind)) build_items(h); else build_tiles(h);
+    h->max_lattice_parts = 0;
+    for (int k = 0; k < h->n_inst; ++k)
+        h->max_lattice_parts =
+            std::max(h->max_lattice_parts, h->inst[k].part_end - h->inst[k].part_begin);
     cudaError_t e = cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(Inst) * h->n_inst,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -520,6 +538,9 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
     h->d_macc = reinterpret_cast<double*>(h->ws + h->layout.macc_off);
     h->d_frz = reinterpret_cast<double*>(h->ws + h->layout.frz_off);
     h->d_prof = reinterpret_cast<double*>(h->ws + h->layout.prof_off);
+    h->d_prof_out = reinterpret_cast<double*>(h->ws + h->layout.prof_out_off);
+    h->d_red = reinterpret_cast<double*>(h->ws + h->layout.red_off);
+    h->d_cnt = reinterpret_cast<unsigned*>(h->ws + h->layout.cnt_off);
     h->mdot_base.assign(n_inst, 0.0);
     h->frz_base.assign(n_inst, 0.0);
     h->step0.assign(n_inst, 0);
@@ -532,7 +553,7 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
         cudaGetLastError();
     }
     if (cudaMemsetAsync(h->d_sync, 0, sizeof(SyncBlock), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->d_macc, 0, h->layout.frz_off - h->layout.macc_off, h->stream) != cudaSuccess) {
+        cudaMemsetAsync(h->d_macc, 0, h->layout.cnt_end - h->layout.macc_off, h->stream) != cudaSuccess) {
         delete h;
         return LBM_ECUDA;
     }
@@ -627,11 +648,9 @@ int lbm_step(lbm_handle* h, int64_t n) {
         }
     }
     for (int64_t k = 0; k < body + (n > 0 ? 1 : 0); ++k) {
+        // the observable step adds each column's f_s to the profile accumulator,
+        // which the reduction below publishes and zeroes again
         const int obs = (k == body);
-        if (obs) {  // the observable step adds each column's f_s to a zeroed profile
-            cudaError_t e = cudaMemsetAsync(h->d_prof, 0, h->layout.prof_bytes, h->stream);
-            if (e != cudaSuccess) return cuda_fail(e);
-        }
         cudaError_t e = enqueue_step(h, h->parity, obs, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
@@ -639,8 +658,9 @@ int lbm_step(lbm_handle* h, int64_t n) {
         h->steps++;
     }
     if (n > 0) {
-        cudaError_t e = lbmk::launch_reduce_obs(h->d_inst, h->n_inst, h->d_part, h->d_obs, h->d_frz,
-                                                h->clock, h->stream);
+        cudaError_t e = lbmk::launch_reduce_obs(h->d_inst, h->n_inst, h->max_lattice_parts,
+                                                h->d_part, h->d_obs, h->d_frz, h->d_red,
+                                                h->d_cnt, h->clock, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
         h->have_obs = true;
@@ -681,7 +701,7 @@ int lbm_freezing(lbm_handle* h, int32_t inst, double* out) {
 int lbm_solid_profile(lbm_handle* h, int32_t inst, double* out) {
     if (!inst_ok(h, inst) || !out) return LBM_EINVAL;
     if (!h->have_obs) return LBM_ESTATE;
-    cudaError_t e = cudaMemcpyAsync(out, h->d_prof + h->layout.prof_at[inst],
+    cudaError_t e = cudaMemcpyAsync(out, h->d_prof_out + h->layout.prof_at[inst],
                                     sizeof(double) * (size_t)h->params[inst].nx,
                                     cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = sync_checked(h);

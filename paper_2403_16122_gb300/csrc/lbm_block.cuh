@@ -606,7 +606,8 @@ __device__ __forceinline__ bool block_item(const Inst* __restrict__ insts, const
         rO = rN;
     }
 
-    if (OBS && lane < kObs) partials[(long long)lane * I.part_stride + W.part] = ob.total();
+    if (OBS && RowObs::carried(lane) >= 0)
+        partials[(long long)RowObs::carried(lane) * I.part_stride + W.part] = ob.total();
     double* const macc = insts[W.inst].macc;
     if (macc) {
         float v = mdsm[lane];

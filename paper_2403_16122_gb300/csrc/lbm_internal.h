@@ -186,7 +186,9 @@ struct Inst {
     double* macc;             // per tile / strip item (index `part`): sum of mdot over
                               // its sites, accumulated over every step (null: off)
     double* prof;             // nx doubles: sum over y of f_s per column, added to
-                              // by observable steps (zeroed before each; null: off)
+                              // by observable steps (zero before each; null: off)
+    double* prof_out;         // nx doubles: prof as of the last observable step,
+                              // published by the reduction, which re-zeroes prof
     // physics, single precision
     float L, Hs, Tm, Cp, Cpref, Tw;
     float omega_g, omega_h;          // 1 / tau

@@ -406,12 +406,19 @@ struct ObsAcc {
 };
 
 // Observable sums of a warp strip, taken row by row: at the end of each row
-// the values of its sites are summed across the warp (a fixed xor tree in
-// FP32, at most 30 sites), and lane j carries observable j's running sum over
-// the rows with Neumaier's compensation, so a lane keeps two running values
-// instead of 2 kObs. Lanes that update no site contribute zeros; slot 9 is a
-// maximum.
+// the values of its sites (at most 30) are summed across the warp in FP32,
+// and one lane carries each observable's running sum over the rows with
+// Neumaier's compensation, so a lane keeps two running values instead of
+// 2 kObs (the row values are dead between rows). Slots 0-6 go through one
+// reduce-scatter: at each of lane bits 4, 3 and 2 a lane keeps half of its
+// vector and adds the partner's copy of that half, then two xor steps finish
+// the sums, and lane L holds the warp total of slot (L >> 2) & 7 (7 is
+// padding). Slot 9 (a maximum) takes its own xor tree; slots 7, 8 and 10 are
+// zero on all but a few rows, and their tree runs only when a lane holds a
+// nonzero value (skipping it adds nothing). Lanes that update no site
+// contribute zeros. The order of every sum is fixed by the lane indices.
 struct RowObs {
+    static_assert(kObs == 11, "slot assignment below");
     float v[kObs];
     float s, c;
     __device__ __forceinline__ void zero() {
@@ -422,26 +429,49 @@ struct RowObs {
     }
     __device__ __forceinline__ void add(int j, float x) { v[j] += x; }
     __device__ __forceinline__ void max(int j, float x) { v[j] = fmaxf(v[j], x); }
+    // the observable lane `lane` carries (-1: none)
+    static __device__ __forceinline__ int carried(int lane) {
+        if ((lane & 3) == 0) return lane < 28 ? lane >> 2 : -1;
+        return lane == 1 ? 9 : (lane == 2 ? 7 : (lane == 3 ? 8 : (lane == 5 ? 10 : -1)));
+    }
+    static __device__ __forceinline__ float warp_sum(float t) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        return t;
+    }
     // all 32 lanes, once per row
     __device__ __forceinline__ void flush(int lane) {
-        float mine = 0.f;
+        constexpr unsigned kAll = 0xffffffffu;
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+        float k4[4], k2[2];
 #pragma unroll
-        for (int j = 0; j < kObs; ++j) {
-            float t = v[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float u = __shfl_xor_sync(0xffffffffu, t, o);
-                t = (j == 9) ? fmaxf(t, u) : t + u;
-            }
-            mine = lane == j ? t : mine;
-            v[j] = 0.f;
+        for (int q = 0; q < 4; ++q) {
+            const float lo = v[q], hi = q + 4 < 7 ? v[q + 4] : 0.f;
+            k4[q] = (b4 ? hi : lo) + __shfl_xor_sync(kAll, b4 ? lo : hi, 16);
         }
-        if (lane == 9) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            k2[q] = (b3 ? k4[q + 2] : k4[q]) + __shfl_xor_sync(kAll, b3 ? k4[q] : k4[q + 2], 8);
+        float t = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(kAll, b2 ? k2[0] : k2[1], 4);
+        t += __shfl_xor_sync(kAll, t, 2);
+        t += __shfl_xor_sync(kAll, t, 1);
+        float mx = v[9];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kAll, mx, o));
+        float x7 = 0.f, x8 = 0.f, x10 = 0.f;
+        if (__any_sync(kAll, v[7] != 0.f)) x7 = warp_sum(v[7]);
+        if (__any_sync(kAll, v[8] != 0.f)) x8 = warp_sum(v[8]);
+        if (__any_sync(kAll, v[10] != 0.f)) x10 = warp_sum(v[10]);
+        const float mine = (lane & 3) == 0 ? t
+                           : (lane == 1 ? mx : (lane == 2 ? x7 : (lane == 3 ? x8 : (lane == 5 ? x10 : 0.f))));
+#pragma unroll
+        for (int j = 0; j < kObs; ++j) v[j] = 0.f;
+        if (lane == 1) {
             s = fmaxf(s, mine);
         } else {
-            const float t = s + mine;
-            c += fabsf(s) >= fabsf(mine) ? (s - t) + mine : (mine - t) + s;
-            s = t;
+            const float u = s + mine;
+            c += fabsf(s) >= fabsf(mine) ? (s - u) + mine : (mine - u) + s;
+            s = u;
         }
     }
     __device__ __forceinline__ double total() const { return (double)s + (double)c; }
@@ -1491,7 +1521,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     }
     if constexpr (STG > 0) cp_async_wait<0>();  // the trailing groups are empty
 
-    if (OBS && lane < kObs) partials[(long long)lane * I.part_stride + W.part] = ob.total();
+    if (OBS && RowObs::carried(lane) >= 0)
+        partials[(long long)RowObs::carried(lane) * I.part_stride + W.part] = ob.total();
     // the item's mdot of this step joins its FP64 running sum (one warp owns
     // the item, so the read-modify-write needs no atomic)
     double* const macc = insts[W.inst].macc;  // read here: no register held over the rows
