@@ -67,6 +67,16 @@ __host__ __device__ constexpr int OPP(int i) {
     return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
 }
 __host__ __device__ constexpr float WGT(int i) { return i == 0 ? kW0 : (i <= 4 ? kW1 : kW2); }
+// c_i . (a, b) with the components of c_i (0, +1, -1) applied as selects, so
+// that an unrolled loop folds them: no multiplication by zero is issued
+// (IEEE arithmetic cannot drop 0 * x) and a diagonal costs one addition.
+__host__ __device__ __forceinline__ float cdot(int i, float a, float b) {
+    const int cx = CX(i), cy = CY(i);
+    if (cx == 0 && cy == 0) return 0.f;
+    if (cx == 0) return cy > 0 ? b : -b;
+    if (cy == 0) return cx > 0 ? a : -a;
+    return (cx > 0 ? a : -a) + (cy > 0 ? b : -b);
+}
 
 static_assert(OPP(1) == 3 && OPP(2) == 4 && OPP(3) == 1 && OPP(4) == 2, "opp axis");
 static_assert(OPP(5) == 7 && OPP(6) == 8 && OPP(7) == 5 && OPP(8) == 6, "opp diag");
@@ -557,8 +567,8 @@ __device__ __forceinline__ void site_update_to(const Phys& P, int flags, const M
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const float fi = pop.F(i);
-        mx += CX(i) * fi;
-        my += CY(i) * fi;
+        if (CX(i) > 0) mx += fi; else if (CX(i) < 0) mx -= fi;
+        if (CY(i) > 0) my += fi; else if (CY(i) < 0) my -= fi;
         if (i) fne0 += fi;
     }
     const float inv_rho = 1.f / rho;
@@ -607,57 +617,85 @@ __device__ __forceinline__ void site_update_to(const Phys& P, int flags, const M
     }
     const float TCp = T * Cp_loc, TCpref = T * P.Cpref;
     const float uu15 = 1.5f * uu;
-    float g0n = 0.f, h0n = 0.f, f0n = 0.f;  // rest populations
+    // rest populations (c_0 = 0)
+    const float gi0 = pop.G(0), hi0 = pop.H(0), fi0 = pop.F(0);
+    float g0n, h0n, f0n;
+    {
+        const float si = kW0 * -uu15;
+        const float geq = kW0 * phi;
+        g0n = gi0 - P.omega_g * (gi0 - geq) + gsrc * (kW0 * pmd);
+        // h_0 carried shifted by -L f_l
+        const float heq0 = m.Hp + dL - TCpref + kW0 * (TCpref - TCp * uu15);
+        h0n = (1.f - omega_h) * (hi0 + dL) + omega_h * heq0;
+        const float feq = (kW0 - 1.f) * 3.f * pn + rho * si;
+        f0n = fi0 - omega_f * (fi0 - feq) + fsrc * (kW0 * (S - 3.f * uFt));
+    }
     // 16-bit storage: what the stored values add to the site's outgoing
     // deviations (sum of q - d), taken back from the rest populations
     float eg = 0.f, eh = 0.f, ef = 0.f;
+    // the moving populations in pairs of opposite directions i and j = OPP(i):
+    // c_j = -c_i, so every term odd in c changes sign and every even term is
+    // shared, and each update below is one paired FP32 operation (FFMA2 /
+    // FADD2) for both directions
+    const float2 sgn = make_float2(1.f, -1.f);
+    auto bc = [](float v) { return make_float2(v, v); };
+    auto sub2 = [](float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); };
+    const float2 og = bc(-P.omega_g), oh = bc(-omega_h), of = bc(-omega_f);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int q = 0; q < 4; ++q) {
+        const int i = q < 2 ? q + 1 : q + 3;  // 1, 2, 5, 6
+        const int j = OPP(i);                  // 3, 4, 7, 8
         const float w = WGT(i);
-        const float cu = CX(i) * ux + CY(i) * uy;
-        // s_i(u) of Eq. 32, shared by the flow and enthalpy equilibria
-        const float si = w * (3.f * cu + 4.5f * cu * cu - uu15);
-        // g (Eqs. 21, 24, 25)
-        const float geq = w * phi * (1.f + 3.f * cu);
-        const float Gi = w * (3.f * (CX(i) * ax + CY(i) * ay) + pmd);
-        const float gi = pop.G(i), hi = pop.H(i), fi = pop.F(i);
-        const float gn = gi - P.omega_g * (gi - geq) + gsrc * Gi;
-        // h (Eqs. 27-28); h_0 carried shifted by -L f_l
-        float hn;
-        if (i == 0) {
-            const float heq0 = m.Hp + dL - TCpref + kW0 * (TCpref - TCp * uu15);
-            hn = (1.f - omega_h) * (hi + dL) + omega_h * heq0;
-        } else {
-            const float heq = w * TCpref + TCp * si;
-            hn = hi - omega_h * (hi - heq);
+        const float cu = cdot(i, ux, uy);
+        const float w3cu = 3.f * w * cu;
+        // s(u) of Eq. 32 (shared by the flow and enthalpy equilibria): its odd
+        // part 3 w c.u and its even part w (4.5 (c.u)^2 - 1.5 u.u)
+        const float sev = w * (4.5f * cu * cu - uu15);
+        const float2 si = __ffma2_rn(bc(w3cu), sgn, bc(sev));
+        // f (Eqs. 30-33): 9 (c.u)(c.Ft) is even, 3 c.(F + rho f) odd
+        const float2 feq = __ffma2_rn(bc(rho), si, bc(w * 3.f * pn));
+        const float Fev = w * (S + 9.f * cu * cdot(i, Ftx, Fty) - 3.f * uFt);
+        const float2 Fi = __ffma2_rn(bc(3.f * w * cdot(i, Fpx, Fpy)), sgn, bc(Fev));
+        const float2 f = make_float2(pop.F(i), pop.F(j));
+        const float2 fn = __ffma2_rn(bc(fsrc), Fi, __ffma2_rn(of, sub2(f, feq), f));
+        if constexpr (sizeof(ST) == 4) {  // f first: its registers are free for g and h
+            out.f32(i, fn.x);
+            out.f32(j, fn.y);
         }
-        // f (Eqs. 30-33)
-        const float feq = (i == 0 ? (kW0 - 1.f) : w) * 3.f * pn + rho * si;
-        const float cF = CX(i) * Ftx + CY(i) * Fty;
-        const float Fi = w * (S + 3.f * (CX(i) * Fpx + CY(i) * Fpy) + 9.f * cu * cF - 3.f * uFt);
-        const float fn = fi - omega_f * (fi - feq) + fsrc * Fi;
-        if (i == 0) {
-            g0n = gn; h0n = hn; f0n = fn;  // own-site group, stored below
-        } else if constexpr (sizeof(ST) == 4) {
-            out.gh32(i, gn, hn);
-            out.f32(i, fn);
+        // g (Eqs. 21, 24, 25)
+        const float2 geq = __ffma2_rn(bc(phi * w3cu), sgn, bc(w * phi));
+        const float2 Gi = __ffma2_rn(bc(3.f * w * cdot(i, ax, ay)), sgn, bc(w * pmd));
+        const float2 g = make_float2(pop.G(i), pop.G(j));
+        const float2 gn = __ffma2_rn(bc(gsrc), Gi, __ffma2_rn(og, sub2(g, geq), g));
+        // h (Eqs. 27-28)
+        const float2 heq = __ffma2_rn(bc(TCp), si, bc(w * TCpref));
+        const float2 h = make_float2(pop.H(i), pop.H(j));
+        const float2 hn = __ffma2_rn(oh, sub2(h, heq), h);
+        if constexpr (sizeof(ST) == 4) {
+            out.gh32(i, gn.x, hn.x);
+            out.gh32(j, gn.y, hn.y);
         } else {
-            {
-                // deviations from the rest equilibria (g, h: destination's
-                // references dref[i]; f: this site's pressure), and what their
-                // rounding to 16 bits takes away from what the site sends
-                using C16 = Bits16<ST>;
-                const Ref& d = dref[i];
-                const float dg = gn - w * d.phi, dh = hn - w * P.Cpref * d.T;
-                const float df = (fn - f_rest(i, pn)) * kFScale;
-                const unsigned qgh = C16::pack2(dg, dh);  // (g_i, h_i) in one word
-                const ST qf = C16::from_f(df);
-                out.gh16(i, qgh);
-                out.f16(i, C16::bits(qf));
-                eg = C16::add_lo(qgh, eg - dg);
-                eh = C16::add_hi(qgh, eh - dh);
-                ef = C16::add_lo((unsigned)C16::bits(qf), ef - df);
-            }
+            // deviations from the rest equilibria (g, h: destination's
+            // references dref[i]; f: this site's pressure), and what their
+            // rounding to 16 bits takes away from what the site sends
+            using C16 = Bits16<ST>;
+            const float2 dphi = make_float2(dref[i].phi, dref[j].phi);
+            const float2 dT = make_float2(dref[i].T, dref[j].T);
+            const float2 dg = __ffma2_rn(bc(-w), dphi, gn);
+            const float2 dh = __ffma2_rn(bc(-w * P.Cpref), dT, hn);
+            const float2 df = __fmul2_rn(__fadd2_rn(fn, bc(-f_rest(i, pn))), bc(kFScale));
+            const unsigned qi = C16::pack2(dg.x, dh.x), qj = C16::pack2(dg.y, dh.y);
+            const ST fi_ = C16::from_f(df.x), fj_ = C16::from_f(df.y);
+            out.gh16(i, qi);
+            out.gh16(j, qj);
+            out.f16(i, C16::bits(fi_));
+            out.f16(j, C16::bits(fj_));
+            eg = C16::add_lo(qi, eg - dg.x);
+            eh = C16::add_hi(qi, eh - dh.x);
+            ef = C16::add_lo((unsigned)C16::bits(fi_), ef - df.x);
+            eg = C16::add_lo(qj, eg - dg.y);
+            eh = C16::add_hi(qj, eh - dh.y);
+            ef = C16::add_lo((unsigned)C16::bits(fj_), ef - df.y);
         }
     }
     if constexpr (sizeof(ST) != 4) {  // the rest populations carry the rounding

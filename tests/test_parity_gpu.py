@@ -154,12 +154,27 @@ def test_bubbles_masked_surface_tension(oracle_mod):
 @pytest.mark.parametrize("nx,ny,px,py", [(5, 7, 1, 1), (3, 3, 1, 1), (33, 9, 1, 0),
                                          (9, 40, 0, 1), (3, 5, 0, 0)])
 def test_small_and_odd_lattices(oracle_mod, nx, ny, px, py):
-    """Tiny periodic wraps, single-column tails, walls on tiny grids."""
+    """Tiny periodic wraps, single-column tails, walls on tiny grids, from
+    random fields. The FP32 bar assumes a case that does not amplify
+    rounding; a random field in a tiny closed box can: the FP64 oracle itself,
+    started from fields perturbed at FP32 rounding (6e-8 relative), moves its
+    populations by up to 1.2e-5 in 200 steps on the 3 x 5 box. Each case is
+    therefore held to the larger of 1e-5 and three times that measured
+    sensitivity."""
     p = inputs.params(nx=nx, ny=ny, periodic_x=px, periodic_y=py, dirichlet_y_lo=1 - py,
                       dirichlet_x_lo=1 - px, theta_deg=70.0)
     phi0, T0 = inputs.random_state(p, seed=nx * 100 + ny)
     lat, o = _both(oracle_mod, p, phi0, T0, 200)
-    compare_state(lat.get_state(), o.get_state())
+    ref = o.get_state()[0]
+    rng = np.random.default_rng(1)
+    sens = 0.0
+    for _ in range(2):
+        q = oracle_mod.Oracle(p).init(phi0 * (1 + 6e-8 * rng.standard_normal(phi0.shape)),
+                                      T0 * (1 + 6e-8 * rng.standard_normal(T0.shape))).step(200)
+        sens = max(sens, float(np.abs(q.get_state()[0] - ref).max()))
+    tol = max(1e-5, 3.0 * sens)
+    print(nx, ny, px, py, "sensitivity", sens, "tolerance", tol)
+    compare_state(lat.get_state(), o.get_state(), tol_pops=tol)
 
 
 def test_set_state_roundtrip_and_resume(oracle_mod):
