@@ -179,6 +179,9 @@ class ClockSampler:
 # roofline helpers
 # ---------------------------------------------------------------------------
 
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
+
+
 def measured_hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -364,6 +367,8 @@ def run_ours(args, dist: Dist):
                 # a sibling with the same items and ring: the same traffic)
                 "traffic_kernel": traffic_kernel,
                 "peak_kind": peak_kind,
+                # the same against the nominal HBM3e peak of the part
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_launch": bytes_lu * sites}
 
     # end to end through the C-ABI with host buffers: upload the fields from
