@@ -337,6 +337,25 @@ __device__ __forceinline__ void grad_cols(const ColSums& L, const ColSums& C, co
     gx = 3.f * (R.A - L.A);
     gy = 3.f * (kW1 * C.D + kW2 * (R.D + L.D));
 }
+// The same for two fields at once (paired FP32 operations, each component
+// evaluated exactly as above); S2 = p + m is returned for the Laplacian.
+struct ColSums2 {
+    float2 A, D, S2;
+};
+__device__ __forceinline__ ColSums2 col_sums2(float2 m, float2 c, float2 p) {
+    ColSums2 r;
+    r.S2 = __fadd2_rn(p, m);
+    r.A = __ffma2_rn(make_float2(kW1, kW1), c, __fmul2_rn(make_float2(kW2, kW2), r.S2));
+    r.D = __fadd2_rn(p, make_float2(-m.x, -m.y));
+    return r;
+}
+__device__ __forceinline__ void grad_cols2(const ColSums2& L, const ColSums2& C, const ColSums2& R,
+                                           float2& gx, float2& gy) {
+    const float2 k3 = make_float2(3.f, 3.f);
+    gx = __fmul2_rn(k3, __fadd2_rn(R.A, make_float2(-L.A.x, -L.A.y)));
+    gy = __fmul2_rn(k3, __ffma2_rn(make_float2(kW1, kW1), C.D,
+                                   __fmul2_rn(make_float2(kW2, kW2), __fadd2_rn(R.D, L.D))));
+}
 // cL, cR: row-y values of the side columns; sL, sC, sR: p + m of each column
 __device__ __forceinline__ float lap_cols(float cL, float cC, float cR, float sL, float sC,
                                           float sR) {
@@ -1477,21 +1496,25 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
         // Eq. 38 from column sums exchanged with the neighbouring lanes
         Stencil st;
         {
-            const float sph = php + phm;
-            const ColSums cph = col_sums(phm, ph0, php), crh = col_sums(rhm, rh0, rhp);
-            const ColSums cpp = col_sums(pm, p0, pp), cSS = col_sums(Sm, S0, Sp);
-            auto side = [](const ColSums& v, int dx) {
-                ColSums r;
-                r.A = lane_shift(v.A, dx);
-                r.D = lane_shift(v.D, dx);
+            // (phi, rho) and (p, S) in pairs
+            const ColSums2 c1 = col_sums2(make_float2(phm, rhm), make_float2(ph0, rh0),
+                                          make_float2(php, rhp));
+            const ColSums2 c2 = col_sums2(make_float2(pm, Sm), make_float2(p0, S0),
+                                          make_float2(pp, Sp));
+            auto side = [](const ColSums2& v, int dx) {
+                ColSums2 r;
+                r.A = make_float2(lane_shift(v.A.x, dx), lane_shift(v.A.y, dx));
+                r.D = make_float2(lane_shift(v.D.x, dx), lane_shift(v.D.y, dx));
                 return r;
             };
-            grad_cols(side(cph, -1), cph, side(cph, 1), st.gphx, st.gphy);
+            float2 gx, gy;
+            grad_cols2(side(c1, -1), c1, side(c1, 1), gx, gy);
+            st.gphx = gx.x; st.gphy = gy.x; st.grx = gx.y; st.gry = gy.y;
+            const float sph = c1.S2.x;  // php + phm
             st.lph = lap_cols(lane_shift(ph0, -1), ph0, lane_shift(ph0, 1), lane_shift(sph, -1),
                               sph, lane_shift(sph, 1));
-            grad_cols(side(crh, -1), crh, side(crh, 1), st.grx, st.gry);
-            grad_cols(side(cpp, -1), cpp, side(cpp, 1), st.gpx, st.gpy);
-            grad_cols(side(cSS, -1), cSS, side(cSS, 1), st.gSx, st.gSy);
+            grad_cols2(side(c2, -1), c2, side(c2, 1), gx, gy);
+            st.gpx = gx.x; st.gpy = gy.x; st.gSx = gx.y; st.gSy = gy.y;
         }
 
         // FP16 storage: references of the sites each outgoing population
