@@ -29,6 +29,7 @@
 #include <cuda_fp16.h>
 
 #include "lbm_internal.h"
+#include "lbm_math.cuh"
 
 // The build compiles this file once per part, each compilation whole (nvcc's
 // own partitioning of a file for parallel compilation makes the code of a
@@ -259,7 +260,7 @@ __device__ __forceinline__ Macro local_macro(const Phys& P, const float g[9], co
     const float chi = clamp01((phihat - 0.5f) * P.inv_ramp + 0.5f);
     const float fs = chi * (1.0f - fl);
     const float mdot = P.mdot_coef * chi * (flp - fl);   // Eq. 19, phase change only
-    const float phi = phihat / (1.0f - 0.5f * mdot);    // Eq. 26
+    const float phi = div_normal(phihat, 1.0f - 0.5f * mdot);    // Eq. 26
     m.Hp = Hp; m.fl = fl; m.flp = flp; m.fs = fs; m.mdot = mdot; m.phi = phi;
     m.rho = mix3(fs, phi, P.rho_s, P.rho_l, P.rho_g);   // Eq. 1
     // Eq. 9b on the shifted enthalpy, H - H_s - L f_l = H' - H_s + L (f_l^{n-1}
@@ -590,7 +591,7 @@ __device__ __forceinline__ void site_update_to(const Phys& P, int flags, const M
         if (CY(i) > 0) my += fi; else if (CY(i) < 0) my -= fi;
         if (i) fne0 += fi;
     }
-    const float inv_rho = 1.f / rho;
+    const float inv_rho = div_normal(1.f, rho);
     const float usx = (mx + 0.5f * Fx) * inv_rho, usy = (my + 0.5f * Fy) * inv_rho;
     const float ffx = -fs * usx, ffy = -fs * usy;
     const float ux = usx + 0.5f * ffx, uy = usy + 0.5f * ffy;
@@ -603,7 +604,7 @@ __device__ __forceinline__ void site_update_to(const Phys& P, int flags, const M
     const float uFt = ux * Ftx + uy * Fty;
     const float mu = mix3(fs, phi, P.mu_s, P.mu_l, P.mu_g);
     const float tau_f = 3.f * mu * inv_rho + 0.5f;
-    const float omega_f = 1.f / tau_f;
+    const float omega_f = div_normal(1.f, tau_f);
     const float Fpx = Fx + rho * ffx, Fpy = Fy + rho * ffy;  // F + rho f
     const float F0 = kW0 * (S - 3.f * uFt);
     // Eq. 36 with s_0(u) = -w_0 u.u / (2 c_s^2); the F_0 correction is the
