@@ -174,6 +174,8 @@ struct lbm_handle {
     double* d_part = nullptr;
     double* d_obs = nullptr;
     double* h_obs = nullptr;   // pinned host mirror of d_obs (null: copy to the caller directly)
+    double* d_obs_map = nullptr;  // h_obs as the device sees it when mapped: the reduction
+                                  // writes the records there too (no copy per read)
     double* d_stage = nullptr;
     double* d_macc = nullptr;  // running mdot sum per partial slot
     double* d_frz = nullptr;   // freezing records (kFrz doubles per lattice)
@@ -484,6 +486,11 @@ bool unstable(const double* rec) {
 // through the pinned mirror (the driver stages a copy into pageable memory
 // with an extra synchronisation), then the synchronising check.
 cudaError_t read_obs(lbm_handle* h, size_t off, size_t n, double* out) {
+    if (h->d_obs_map) {  // the reduction wrote the records into host memory itself
+        cudaError_t e = sync_checked(h);
+        if (e == cudaSuccess) memcpy(out, h->h_obs + off, n * sizeof(double));
+        return e;
+    }
     double* dst = h->h_obs ? h->h_obs + off : out;
     cudaError_t e = cudaMemcpyAsync(dst, h->d_obs + off, n * sizeof(double), cudaMemcpyDeviceToHost,
                                     h->stream);
@@ -548,7 +555,14 @@ int lbm_create(const lbm_params* p, int32_t n_inst, int32_t storage, void* d_wor
         h->h_frz = nullptr;  // the records are then copied to the caller's memory directly
         cudaGetLastError();
     }
-    if (cudaMallocHost(&h->h_obs, sizeof(double) * lbmk::kObs * n_inst) != cudaSuccess) {
+    if (cudaHostAlloc(&h->h_obs, sizeof(double) * lbmk::kObs * n_inst, cudaHostAllocMapped) ==
+        cudaSuccess) {
+        if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->d_obs_map), h->h_obs, 0) !=
+            cudaSuccess) {
+            h->d_obs_map = nullptr;  // copied per read instead
+            cudaGetLastError();
+        }
+    } else if (cudaMallocHost(&h->h_obs, sizeof(double) * lbmk::kObs * n_inst) != cudaSuccess) {
         h->h_obs = nullptr;  // the observables are then copied to the caller's memory directly
         cudaGetLastError();
     }
@@ -659,8 +673,8 @@ int lbm_step(lbm_handle* h, int64_t n) {
     }
     if (n > 0) {
         cudaError_t e = lbmk::launch_reduce_obs(h->d_inst, h->n_inst, h->max_lattice_parts,
-                                                h->d_part, h->d_obs, h->d_frz, h->d_red,
-                                                h->d_cnt, h->clock, h->stream);
+                                                h->d_part, h->d_obs, h->d_obs_map, h->d_frz,
+                                                h->d_red, h->d_cnt, h->clock, h->stream);
         h->launches++;
         if (e != cudaSuccess) return cuda_fail(e);
         h->have_obs = true;

@@ -32,7 +32,8 @@ __device__ __forceinline__ double combine(int j, double a, double b) {
 // zeroes the accumulator for the next observable step) and re-arms the count.
 __global__ void __launch_bounds__(kPer)
 reduce_obs_split(const Inst* __restrict__ insts, const double* __restrict__ partials,
-                 double* __restrict__ out, double* __restrict__ frz, double* __restrict__ scratch,
+                 double* __restrict__ out, double* __restrict__ out_host,
+                 double* __restrict__ frz, double* __restrict__ scratch,
                  unsigned* __restrict__ counts, long long step) {
     // value q of a row sits at q + q / kGroup: the first-level readers of one
     // warp (one group each) then hit distinct banks
@@ -97,7 +98,10 @@ reduce_obs_split(const Inst* __restrict__ insts, const double* __restrict__ part
     }
     if (t < kSums) {
         g1[t][0] = tot;
-        if (t < kObs) out[(long long)k * kObs + t] = tot;
+        if (t < kObs) {
+            out[(long long)k * kObs + t] = tot;
+            if (out_host) out_host[(long long)k * kObs + t] = tot;
+        }
     }
     if (I.prof && I.prof_out) {
         double* const acc = I.prof;
@@ -136,9 +140,9 @@ reduce_obs_split(const Inst* __restrict__ insts, const double* __restrict__ part
 int reduce_slots(int max_parts, int n_inst) { return max_parts / kPer + n_inst + 1; }
 
 cudaError_t launch_reduce_obs(const Inst* d_inst, int n_inst, int max_lattice_parts,
-                              const double* d_partials, double* d_obs, double* d_frz,
-                              double* d_scratch, unsigned* d_counts, long long step,
-                              cudaStream_t s) {
+                              const double* d_partials, double* d_obs, double* d_obs_host,
+                              double* d_frz, double* d_scratch, unsigned* d_counts,
+                              long long step, cudaStream_t s) {
     if (n_inst <= 0) return cudaSuccess;
     const int per = (max_lattice_parts + kPer - 1) / kPer;
     cudaLaunchConfig_t cfg = {};
@@ -150,8 +154,8 @@ cudaError_t launch_reduce_obs(const Inst* d_inst, int n_inst, int max_lattice_pa
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, reduce_obs_split, d_inst, d_partials, d_obs, d_frz, d_scratch,
-                              d_counts, step);
+    return cudaLaunchKernelEx(&cfg, reduce_obs_split, d_inst, d_partials, d_obs, d_obs_host, d_frz,
+                              d_scratch, d_counts, step);
 }
 
 }  // namespace lbmk
