@@ -287,8 +287,9 @@ int lbm_get_kernel(const lbm_handle* h, int32_t* out);
 /* Autotuner: time every supported layout for this handle twice over `steps`
    time steps each (after one warm-up step), measured with CUDA events on the
    stream, and keep the one with the shortest time. The lattices are advanced by every step it
-   runs (lbm_step_count grows accordingly); all layouts compute identical
-   results, so the trajectory is the one lbm_step would have produced.
+   runs (lbm_step_count grows accordingly); the layouts compute the same
+   update and agree to FP32 rounding, so the trajectory is the one lbm_step
+   would have produced up to that rounding.
    times_ms (may be NULL) receives up to `cap` mean step times in the order
    the candidates were tried; *n_tried their number. Synchronises. */
 int lbm_autotune(lbm_handle* h, int32_t steps, double* times_ms, int32_t cap, int32_t* n_tried);
