@@ -482,9 +482,11 @@ bool unstable(const double* rec) {
     return rec[LBM_OBS_NONFINITE] > 0 || rec[LBM_OBS_UMAX] > kMaxSpeed;
 }
 
-// n doubles of the observable records from offset off to the caller's out,
-// through the pinned mirror (the driver stages a copy into pageable memory
-// with an extra synchronisation), then the synchronising check.
+// n doubles of the observable records from offset off to the caller's out:
+// when the mirror is mapped, the reduction has written it and a synchronising
+// check suffices; otherwise a copy into the pinned mirror (a copy straight
+// into pageable memory would be staged by the CUDA runtime with an extra
+// synchronisation), then the check.
 cudaError_t read_obs(lbm_handle* h, size_t off, size_t n, double* out) {
     if (h->d_obs_map) {  // the reduction wrote the records into host memory itself
         cudaError_t e = sync_checked(h);
