@@ -1415,8 +1415,8 @@ __device__ __forceinline__ void strip_item(const Inst* __restrict__ insts, const
     Macro mO;
     Ref rO;
     if constexpr (STG > 0) {
-#pragma unroll
-        for (int j = 0; j < STG; ++j) issue(j);
+#pragma unroll 1
+        for (int j = 0; j < STG; ++j) issue(j);  // one copy of the row issue code
         cp_async_wait<STG - 2>();  // ring indices 0 and 1 have landed
         row_macro_staged(1, y0, mO, p0, S0, rO);
     } else {
