@@ -1996,12 +1996,12 @@ struct Staged {
 // budget): the ring depth follows from what the register budget leaves
 // resident per SM, keeping every variant's shared memory within ~210 KB/SM.
 template <typename ST, typename F>
-auto staged_dispatch(int warps, int regs, F&& f) -> decltype(f(Staged<4, 3, 4, ST>())) {
+auto staged_dispatch(int warps, int regs, F&& f) -> decltype(f(Staged<4, 3, 3, ST>())) {
     if (warps == 4 && regs == 128) return f(Staged<4, 4, 3, ST>());
     if (warps == 4 && regs == 255) return f(Staged<4, 2, 5, ST>());
     if (warps == 8 && regs == 128) return f(Staged<8, 2, 3, ST>());
     if (warps == 2 && regs == 128) return f(Staged<2, 8, 3, ST>());
-    return f(Staged<4, 3, 4, ST>());
+    return f(Staged<4, 3, 3, ST>());
 }
 
 // Warps resident at once for a plain strip variant.
@@ -2057,12 +2057,12 @@ struct Persist {
 // Dispatch of a persistent call F over the supported strip variants: the
 // row-staged ones (ring depths of the staged kernels) and the plain ones.
 template <typename ST, typename F>
-auto persist_dispatch_staged(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 4, ST>())) {
+auto persist_dispatch_staged(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 3, ST>())) {
     if (warps == 4 && regs == 128) return f(Persist<4, 4, 3, ST>());
     if (warps == 4 && regs == 255) return f(Persist<4, 2, 5, ST>());
     if (warps == 8 && regs == 128) return f(Persist<8, 2, 3, ST>());
     if (warps == 2 && regs == 128) return f(Persist<2, 8, 3, ST>());
-    return f(Persist<4, 3, 4, ST>());
+    return f(Persist<4, 3, 3, ST>());
 }
 template <typename ST, typename F>
 auto persist_dispatch_plain(int warps, int regs, F&& f) -> decltype(f(Persist<4, 3, 0, ST>())) {
@@ -2089,14 +2089,14 @@ cudaError_t launch_strip_st(int warps, int regs, const Inst* d_inst, const Item*
 // BF16 storage is built for the two four-warp staged variants only.
 using bf16 = __nv_bfloat16;
 template <typename F>
-auto staged_dispatch_bf16(int regs, F&& f) -> decltype(f(Staged<4, 3, 4, bf16>())) {
+auto staged_dispatch_bf16(int regs, F&& f) -> decltype(f(Staged<4, 3, 3, bf16>())) {
     if (regs == 128) return f(Staged<4, 4, 3, bf16>());
-    return f(Staged<4, 3, 4, bf16>());
+    return f(Staged<4, 3, 3, bf16>());
 }
 template <typename F>
-auto persist_dispatch_bf16(int regs, F&& f) -> decltype(f(Persist<4, 3, 4, bf16>())) {
+auto persist_dispatch_bf16(int regs, F&& f) -> decltype(f(Persist<4, 3, 3, bf16>())) {
     if (regs == 128) return f(Persist<4, 4, 3, bf16>());
-    return f(Persist<4, 3, 4, bf16>());
+    return f(Persist<4, 3, 3, bf16>());
 }
 
 // Block launches: the (warps, regs) variants.

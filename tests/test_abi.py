@@ -116,8 +116,8 @@ def test_step_kernels_keep_their_state_in_registers(lib):
     if not any("step_strip_staged" in k for k in rep):
         lbm_build.build(force=True)  # a library built before the report was kept
         rep = lbm_build.ptxas_report()
-    want = ["ILi4ELi4ELi3ELb0EfE", "ILi4ELi3ELi4ELb0EfE", "ILi4ELi3ELi4ELb1EfE",
-            "ILi4ELi3ELi4ELb0E6__halfE", "ILi4ELi3ELi4ELb1E6__halfE"]
+    want = ["ILi4ELi4ELi3ELb0EfE", "ILi4ELi3ELi3ELb0EfE", "ILi4ELi3ELi3ELb1EfE",
+            "ILi4ELi3ELi3ELb0E6__halfE", "ILi4ELi3ELi3ELb1E6__halfE"]
     for tag in want:
         hits = [v for k, v in rep.items() if "step_strip_staged" + tag in k]
         assert len(hits) == 1, tag
