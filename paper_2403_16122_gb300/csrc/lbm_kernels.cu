@@ -1129,6 +1129,14 @@ __device__ __forceinline__ void cp_async_p(float* dst_smem, const float* src,
                  "l"(src), "n"(N), "l"(pol)
                  : "memory");
 }
+// 16-byte copies that bypass L1 (data no other copy of the warp reads again).
+__device__ __forceinline__ void cp_async_cg16(float* dst_smem, const float* src,
+                                              unsigned long long pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "l"(pol)
+                 : "memory");
+}
 // L2 priority of a staged row: 1 keep (evict last), 2 release (evict first),
 // otherwise normal.
 __device__ __forceinline__ unsigned long long l2_policy(int hint) {
@@ -1185,8 +1193,9 @@ __device__ __forceinline__ void stage_row(const LatT<NC>& l, int lane, const Col
     const int t0 = rr * nxb * kPopBlock, tm = ym * nxb * kPopBlock, tp = yp * nxb * kPopBlock;
     const int ra = rr * nxb * kAuxBlock;
     const unsigned long long pol = l2_policy(hint);
-    cp_async_p<16>(slot + 4 * lane, l.Aaux + ra + ct.aux, pol);
-    cp_async_p<16>(slot + kSlotO1 + 4 * lane, l.Aaux + ra + ct.aux + 128, pol);
+    // the site's own values: read by this lane only, so past L1
+    cp_async_cg16(slot + 4 * lane, l.Aaux + ra + ct.aux, pol);
+    cp_async_cg16(slot + kSlotO1 + 4 * lane, l.Aaux + ra + ct.aux + 128, pol);
     if constexpr (kHalf) cp_async_p<8>(slot + kSlotR + 2 * lane, l.Aaux + ra + ct.ref, pol);
     const unsigned short* A16 = reinterpret_cast<const unsigned short*>(l.A);
 #pragma unroll
